@@ -1,0 +1,412 @@
+"""Benchmark of the VBDR hot path on GB300: one step = one time slice of the
+trace workload (k = 30, 64M (aip, bip) pairs per slice, 1M Zipf(1.05) hosts
+with cardinalities 1..2M, 10% in-slice repeats, Z = 2^24 BDRs, g = 256):
+scan the slice, close it (slide), estimate every host.
+
+Prints one JSON line (see the repository's design notes for every key).
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--layout gfast|gsmall] [--workload trace|small]
+Under torchrun (N > 1) every rank runs an independent replica (its own pool
+and traffic): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import traffic  # noqa: E402
+
+SEED = 0x9E3779B97F4A7C15
+N_DISTINCT_SLICES = 4  # distinct device-resident slices, cycled through
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--layout", default="gfast", choices=["gfast", "gsmall"])
+    p.add_argument("--workload", default="trace", choices=["trace", "small"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-mre", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--pairs", type=int, default=0, help="override pairs per slice (profiling)")
+    p.add_argument("--slices", type=int, default=N_DISTINCT_SLICES,
+                   help="distinct device-resident slices cycled through")
+    return p.parse_args()
+
+
+def _workload(name):
+    return dict(traffic.TRACE if name == "trace" else traffic.SMALL)
+
+
+def _metric_name():
+    return "G IP pairs/s scanned + slide/estimate ms per slice; HBM roofline fraction; MRE vs exact"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    dist.init_process_group("nccl")
+    return dist, dist.get_rank(), ws
+
+
+def _barrier_max(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _make_inputs(wl, seed, n_slices):
+    gen = traffic.ZipfTraffic(wl["n_hosts"], wl["zipf_s"], wl["c_max"], wl["k"], seed=seed,
+                              repeat_frac=wl["repeat_frac"])
+    slices = [gen.next_slice(wl["n_pairs"]) for _ in range(n_slices)]
+    return gen, slices
+
+
+def _exact_mre(gen, slices, est_fn, n_sample=20000, seed=3):
+    """MRE against the exact distinct counts (Definition 1) of a host sample:
+    the top 1000 hosts plus uniformly drawn others.  After at least
+    N_DISTINCT_SLICES <= k slices the window holds exactly the union of the
+    distinct slices."""
+    rng = np.random.default_rng(seed)
+    H = gen.aips.size
+    idx = np.unique(np.concatenate([np.arange(min(1000, H)),
+                                    rng.choice(H, size=min(n_sample, H), replace=False)]))
+    sample = gen.aips[idx]
+    srt = np.sort(sample)
+    keys = []
+    for s in slices:
+        a = s[:, 0]
+        pos = np.minimum(np.searchsorted(srt, a), srt.size - 1)
+        m = srt[pos] == a
+        keys.append((a[m].astype(np.uint64) << np.uint64(32)) | s[m, 1].astype(np.uint64))
+    uk = np.unique(np.concatenate(keys))
+    hosts, cnt = np.unique((uk >> np.uint64(32)).astype(np.uint32), return_counts=True)
+    truth = np.zeros(sample.size)
+    pos = np.searchsorted(hosts, sample)
+    ok = (pos < hosts.size) & (hosts[np.minimum(pos, hosts.size - 1)] == sample)
+    truth[ok] = cnt[pos[ok]]
+    est = est_fn(sample)
+    live = truth > 0
+    rel = np.abs(est[live] - truth[live]) / truth[live]
+    big = truth > 100_000
+    small = live & (truth < 1000)
+    out = {"mre": float(rel.mean()), "hosts": int(live.sum())}
+    if big.any():
+        out["p99_rel_err_card_gt_1e5"] = float(np.quantile(np.abs(est[big] - truth[big]) / truth[big], 0.99))
+    if small.any():
+        out["p99_rel_err_card_lt_1e3"] = float(np.quantile(np.abs(est[small] - truth[small]) / truth[small], 0.99))
+    return out
+
+
+# ----------------------------------------------------------------- our arm
+
+def run_ours(a):
+    import torch
+    from paper_1810_13132_gb300 import Config, Vbdr
+
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    wl = _workload(a.workload)
+    if a.pairs:
+        wl["n_pairs"] = a.pairs
+        wl["name"] += f" (profiling: {a.pairs} pairs per slice)"
+    N, H = wl["n_pairs"], wl["n_hosts"]
+    nsl = max(1, a.slices)
+    gen, slices = _make_inputs(wl, seed=1000 + rank, n_slices=nsl)
+    d_slices = [torch.from_numpy(s.view(np.int32)).cuda() for s in slices]
+    d_aips = torch.from_numpy(gen.aips.view(np.int32)).cuda()
+    d_out = torch.empty(H, dtype=torch.float32, device="cuda")
+    v = Vbdr(Config(k=wl["k"], num_bdr=wl["Z"], log2_g=wl["log2_g"], layout=a.layout, seed=SEED))
+    stream = torch.cuda.current_stream()
+
+    def step(i, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        v.scan(d_slices[i % nsl])
+        if ev is not None:
+            ev[1].record(stream)
+        v.slide()
+        if ev is not None:
+            ev[2].record(stream)
+        v.estimate(d_aips, out=d_out)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(a.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(a.steps):
+            step(a.warmup + i, evs[i])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = _barrier_max(dist, t0.elapsed_time(t1))
+    scan_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    slide_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    est_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    ms_step = total_ms / a.steps
+    value = (N * ws * a.steps) / (total_ms * 1e-3) / 1e9
+
+    # accuracy on the state the timed steps left (window = union of the
+    # distinct slices once k >= N_DISTINCT_SLICES slices have been scanned)
+    mre = None
+    if not a.no_mre and rank == 0 and a.warmup + a.steps >= nsl and nsl <= wl["k"]:
+        def est_fn(sample):
+            return v.estimate(torch.from_numpy(sample.view(np.int32)).cuda()).cpu().numpy()
+        mre = _exact_mre(gen, slices, est_fn)
+
+    # end to end through the host-buffer entry points
+    e2e = None
+    if not a.no_e2e:
+        pinned = [torch.from_numpy(s.view(np.int32)).pin_memory() for s in slices]
+        h_aips = torch.from_numpy(gen.aips.view(np.int32)).pin_memory()
+        h_out = torch.empty(H, dtype=torch.float32).pin_memory()
+        v2 = Vbdr(Config(k=wl["k"], num_bdr=wl["Z"], log2_g=wl["log2_g"], layout=a.layout, seed=SEED))
+
+        def e2e_step(i):
+            v2.scan_host(pinned[i % nsl])
+            v2.slide()
+            v2.estimate_host(h_aips, h_out)
+            torch.cuda.current_stream().synchronize()  # result read back on the host
+
+        for i in range(a.warmup):
+            e2e_step(i)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(a.steps):
+            e2e_step(a.warmup + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = _barrier_max(dist, e0.elapsed_time(e1))
+        e2e = {"value": round((N * ws * a.steps) / (e2e_ms * 1e-3) / 1e9, 3),
+               "unit": "G pairs/s", "h2d_bytes_per_step": 8 * N + 4 * H,
+               "d2h_bytes_per_step": 4 * H, "ms_per_step": round(e2e_ms / a.steps, 3)}
+        v2.close()
+
+    peak, peak_kind = _peaks()
+    Z, P = wl["Z"], v.words
+    scan_bytes = 8 * N
+    slide_bytes = Z * ((4 * P + 4) + (4 * P + 4 + 1)) if a.layout == "gfast" else Z * (4 * P + 4 * P + 1)
+    est_bytes = H * (4 + 4) + Z
+    kern = {"scan": (statistics.mean(scan_ms), scan_bytes),
+            "slide": (statistics.mean(slide_ms), slide_bytes),
+            "estimate": (statistics.mean(est_ms), est_bytes)}
+    dom = max(kern, key=lambda k: kern[k][0])
+    dms, dbytes = kern[dom]
+    achieved = dbytes / (dms * 1e-3) / 1e9
+    traffic_bytes = _ncu_traffic(dom, a.layout, a.workload)
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(wl, gen, slices)
+    clocks = clk.summary()
+    line = {
+        "metric": _metric_name(),
+        "value": round(value, 3), "unit": "G pairs/s",
+        "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl["name"] + f" {a.layout}", "layout": a.layout,
+                   "k": wl["k"], "pairs_per_slice": N, "hosts": H, "Z": Z,
+                   "g": 1 << wl["log2_g"], "repeat_frac": wl["repeat_frac"],
+                   "l2": "inputs larger than L2 (512 MiB per slice, 4 distinct slices cycled)",
+                   "parallelism": f"replicas x{ws}"},
+        "scan_gpairs_per_s": round(N / (statistics.mean(scan_ms) * 1e-3) / 1e9, 3),
+        "scan_ms": round(statistics.mean(scan_ms), 4),
+        "slide_ms": round(statistics.mean(slide_ms), 4),
+        "slide_gbs": round(slide_bytes / (statistics.mean(slide_ms) * 1e-3) / 1e9, 1),
+        "estimate_ms": round(statistics.mean(est_ms), 4),
+        "scan_hbm_frac": round(scan_bytes / (statistics.mean(scan_ms) * 1e-3) / 1e9 / peak, 4),
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic_bytes, "peak_kind": peak_kind},
+        "accuracy": mre,
+        "e2e": e2e,
+        "gpu_launches": 3 * a.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    v.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _ncu_traffic(kernel, layout, workload):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if one exists for this kernel, layout and workload."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            return json.load(f).get(f"{kernel}/{layout}/{workload}")
+    except Exception:
+        return None
+
+
+# ------------------------------------------------- oracle (CPU) timings
+
+def _oracle_step_times(wl, gen, slices, n_pairs_sample, n_hosts_sample):
+    """One step of the single-threaded oracle on a bounded sample: scan
+    n_pairs_sample pairs, a full slide of all Z BDRs, estimates of
+    n_hosts_sample hosts; returns seconds per pair, per slide, per host."""
+    import oracle
+    o = oracle.Oracle("gfast", k=wl["k"], Z=wl["Z"], b=wl["log2_g"], seed=SEED)
+    s = slices[0][:n_pairs_sample]
+    t = time.perf_counter()
+    o.scan(s)
+    t_scan = time.perf_counter() - t
+    t = time.perf_counter()
+    o.slide()
+    t_slide = time.perf_counter() - t
+    hs = gen.aips[:n_hosts_sample]
+    t = time.perf_counter()
+    o.estimate(hs)
+    t_est = time.perf_counter() - t
+    return t_scan / len(s), t_slide, t_est / len(hs)
+
+
+def cpu_baseline(wl, gen, slices):
+    ns, nh = min(4_000_000, wl["n_pairs"]), min(50_000, wl["n_hosts"])
+    per_pair, slide_s, per_host = _oracle_step_times(wl, gen, slices, ns, nh)
+    step_s = per_pair * wl["n_pairs"] + slide_s + per_host * wl["n_hosts"]
+    return {"value": round(wl["n_pairs"] / step_s / 1e9, 6), "unit": "G pairs/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"single-threaded C oracle (gfast): scan of {ns} pairs, one full slide of "
+                      f"Z={wl['Z']} BDRs, estimates of {nh} hosts; step time scaled to "
+                      f"{wl['n_pairs']} pairs and {wl['n_hosts']} hosts",
+            "step_s": round(step_s, 3)}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = _workload(a.workload)
+    gen, slices = _make_inputs(wl, seed=1000, n_slices=1)
+    ns, nh = min(2_000_000, wl["n_pairs"]), min(20_000, wl["n_hosts"])
+    steps = []
+    t_all = time.perf_counter()
+    for i in range(a.warmup + a.steps):
+        per_pair, slide_s, per_host = _oracle_step_times(wl, gen, slices, ns, nh)
+        if i >= a.warmup:
+            steps.append(per_pair * wl["n_pairs"] + slide_s + per_host * wl["n_hosts"])
+    step_s = statistics.mean(steps)
+    value = wl["n_pairs"] / step_s / 1e9
+    line = {
+        "impl": "reference", "metric": _metric_name(), "value": round(value, 6),
+        "unit": "G pairs/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": round(step_s * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl["name"] + " gfast"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "G pairs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: scan of {ns} pairs, full slide of Z={wl['Z']}, "
+                                   f"estimates of {nh} hosts, scaled to the full step"},
+        "e2e": {"value": round(value, 6), "unit": "G pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s": round(time.perf_counter() - t_all, 1),
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -1,0 +1,170 @@
+/*
+ * vbdr.h -- C ABI of the GB300 (sm_103a) VBDR library.
+ *
+ * VBDR ("virtual bit distance recorder", Xu, arXiv 1810.13132) estimates the
+ * cardinality of many hosts under a sliding window of k time slices.  Every
+ * host aip owns a virtual vector of g = 2^b bit distance recorders (BDRs)
+ * drawn from one shared pool BDRP of Z physical BDRs (Sec. 4.1).  A BDR is a
+ * vector of w-bit distance recorders (DRs), one per LBP1 value 1..R: a DR
+ * holds how many slices ago its LBP1 value was recorded, saturating at
+ * 2^w - 1, and is active while it is below k (Sec. 3).
+ *
+ * Per time slice t the caller
+ *   1. streams the slice's (aip, bip) pairs through vbdr_scan_slice (one or
+ *      more calls; Alg. 7 for the gfast layout, Alg. 9 for gsmall),
+ *   2. closes the slice with vbdr_slide (Alg. 6 for gfast; Alg. 8 for
+ *      gsmall) which also extracts every BDR's register (Alg. 2) and the
+ *      pool-wide sums used to remove sharing noise,
+ *   3. asks for estimates with vbdr_estimate (Alg. 3 + Alg. 5 + the virtual
+ *      register sharing HyperLogLog estimator), which cover the window
+ *      W(t-k+1, k) of the last k closed slices (fewer at start-up).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: VBDR_OK (0) or a negative vbdr_status.  A CUDA error
+ *     is sticky: the handle then answers VBDR_ECUDA to every later call
+ *     except vbdr_destroy.
+ *   - "stream" is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls are asynchronous and ordered on that stream; a device
+ *     buffer passed in must stay valid until the stream has passed the call.
+ *   - d_* pointers are device memory (or memory the GPU can address); h_*
+ *     pointers are host memory.  The caller owns every buffer it passes in;
+ *     the handle owns its state and frees it in vbdr_destroy.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ *     Different handles are independent and may run on different streams.
+ *   - The library allocates only in vbdr_create (and on the first host-buffer
+ *     call, see vbdr_scan_slice_host).
+ */
+#ifndef VBDR_H_
+#define VBDR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VBDR_API __attribute__((visibility("default")))
+#else
+#define VBDR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vbdr *vbdr_t;
+
+typedef enum {
+  VBDR_OK = 0,
+  VBDR_EINVAL = -1,   /* bad argument: NULL, misaligned, out of range      */
+  VBDR_ENOMEM = -2,   /* device or host allocation failed                  */
+  VBDR_ECUDA = -3,    /* a CUDA call failed; the handle is now unusable    */
+  VBDR_ERANGE = -4,   /* a size exceeds the handle's capacity              */
+  VBDR_EORDER = -5,   /* call out of order (estimate before first slide)   */
+  VBDR_ETIMEOUT = -6  /* a bounded device wait expired                     */
+} vbdr_status;
+
+/* BDR layouts of Sec. 4.2 / Table 1.
+ *   VBDR_GFAST : DRV plus the bsLBP1 bit string; the scan only ORs one bit
+ *                (Alg. 7), the slide folds the highest set bit (Alg. 6).
+ *   VBDR_GSMALL: DRV only; the scan zeroes a DR in place (Alg. 9), the slide
+ *                ages every DR (Alg. 8).  Smaller state, random RMW of the
+ *                DRV during the scan.                                       */
+typedef enum { VBDR_GFAST = 0, VBDR_GSMALL = 1 } vbdr_layout;
+
+typedef struct {
+  uint32_t k;          /* slices per window, 1..255                         */
+  uint32_t log2_g;     /* b of every host when group_rule = 0, 1..16        */
+  uint32_t log2_g_min; /* smallest b in use (0 = log2_g); R = 32 - b_min    */
+  uint32_t group_rule; /* 0: every host has b = log2_g;
+                          1: host aip has b = log2_g_min + (aip >> 30),
+                             i.e. four groups g = 2^b_min .. 2^(b_min+3);
+                             requires b_min + 3 <= 9                        */
+  uint32_t layout;     /* vbdr_layout                                       */
+  uint32_t reserved;   /* must be 0                                         */
+  uint64_t num_bdr;    /* Z, physical BDRs; must exceed the largest g,
+                          at most 2^32                                      */
+  uint64_t seed;       /* hash seed A0 (Sec. 4.1); A1 is derived from it    */
+} vbdr_config;
+
+/* Create a handle and its device-resident state on the current CUDA device
+ * (InitDR on every DR: all DRs start at 2^w - 1, w = ceil(log2(k+1))).
+ * Device memory: DRV ceil(R / floor(32/w)) * 4 B per BDR, plus 4 B bsLBP1
+ * per BDR for gfast, plus 1 B register per BDR.  Errors: VBDR_EINVAL,
+ * VBDR_ENOMEM, VBDR_ECUDA.  *out is NULL on failure. */
+VBDR_API int vbdr_create(const vbdr_config *cfg, vbdr_t *out);
+
+/* Free all state.  Accepts NULL.  Synchronises the device first. */
+VBDR_API int vbdr_destroy(vbdr_t h);
+
+/* Scan n pairs of the current slice (Sec. 4.2, Alg. 7 for gfast, Alg. 9 for
+ * gsmall; per pair the steps of Alg. 4: hash bip with A1, virtual index =
+ * its left b bits, LBP1 of the rest, physical BDR by Alg. 3).
+ * d_pairs: 2n uint32 on the device, array-of-structs (aip, bip), 16-byte
+ * aligned.  n = 0 is a no-op.  May be called several times per slice; the
+ * result does not depend on the order or split of the pairs.
+ * Errors: VBDR_EINVAL (NULL with n > 0, misaligned), VBDR_ECUDA. */
+VBDR_API int vbdr_scan_slice(vbdr_t h, const uint32_t *d_pairs, uint64_t n,
+                    void *stream);
+
+/* The same as vbdr_scan_slice for pairs in HOST memory: the pairs are copied
+ * to the device in chunks through a staging ring owned by the handle (allocated
+ * on the first call), overlapped with the scan of the previous chunk.
+ * h_pairs should be pinned (cudaHostAlloc / cudaHostRegister) for full copy
+ * speed; pageable memory works but is slower.  The call returns once every
+ * chunk is enqueued; h_pairs must stay valid until the stream has passed it.
+ * Errors: as vbdr_scan_slice, plus VBDR_ENOMEM. */
+VBDR_API int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n,
+                         void *stream);
+
+/* Close the current slice (Sec. 3 and 4.2).
+ *   gfast : every BDR slides all DRs, sets the DR of the highest set bit of
+ *           bsLBP1 (Alg. 6) and clears bsLBP1; then its register is read
+ *           (Alg. 2).
+ *   gsmall: every BDR's register is read (Alg. 2, window just closed), then
+ *           all DRs slide (Alg. 8 for the next slice).
+ * Also computes the pool sums S_Z = sum_j 2^(32 - reg_j) and V_Z = #{reg_j
+ * = 0} over all Z registers.  Errors: VBDR_ECUDA. */
+VBDR_API int vbdr_slide(vbdr_t h, void *stream);
+
+/* Estimate the cardinality of n_hosts hosts over the window of the last k
+ * closed slices (Definition 1, Alg. 5 and the virtual register sharing
+ * estimator n = Z g/(Z-g) (n_g/g - n_Z/Z) with HyperLogLog estimates n_g of
+ * the host's g registers and n_Z of the pool, both with small-range linear
+ * counting; clamped at 0).  Harmonic sums are exact integers; the formula
+ * is evaluated in FP64 and rounded to FP32.
+ * d_aips: n_hosts uint32 host addresses (device); d_out: n_hosts float
+ * (device).  n_hosts = 0 is a no-op.
+ * Errors: VBDR_EINVAL, VBDR_EORDER (no slide yet), VBDR_ECUDA. */
+VBDR_API int vbdr_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts,
+                  float *d_out, void *stream);
+
+/* vbdr_estimate for HOST buffers: h_aips is copied in, h_out is written back
+ * on the stream (valid once the stream has passed the call).  Uses a staging
+ * buffer owned by the handle, grown as needed.  Errors: as vbdr_estimate,
+ * plus VBDR_ENOMEM. */
+VBDR_API int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n_hosts,
+                       float *h_out, void *stream);
+
+/* ---- inspection (tests, debugging); these synchronise the stream ---- */
+
+/* Derived sizes: R (DRs per BDR), w (DR bits), words (32-bit DRV words per
+ * BDR).  Any pointer may be NULL. */
+VBDR_API int vbdr_get_dims(vbdr_t h, uint32_t *R, uint32_t *w, uint32_t *words);
+
+/* Copy the logical state to host memory (any pointer may be NULL):
+ * h_dr [Z][R] uint8 (DR of LBP1 value r+1 at [j][r]), h_bs [Z] uint32
+ * (gfast bsLBP1; zeros for gsmall), h_reg [Z] uint8 registers of the last
+ * slide. */
+VBDR_API int vbdr_copy_state(vbdr_t h, uint8_t *h_dr, uint32_t *h_bs, uint8_t *h_reg,
+                    void *stream);
+
+/* Pool sums of the last slide (see vbdr_slide). */
+VBDR_API int vbdr_copy_pool_sums(vbdr_t h, uint64_t *S_Z, uint64_t *V_Z, void *stream);
+
+/* Human-readable text of a vbdr_status. */
+VBDR_API const char *vbdr_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VBDR_H_ */

@@ -1,0 +1,348 @@
+// api.cu -- the C ABI of include/vbdr.h: argument checks, device state
+// ownership, host-buffer staging, and the state-initialisation kernel.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/vbdr.h"
+#include "vbdr_internal.cuh"
+
+using vbk::DevState;
+using vbk::Dims;
+
+struct vbdr {
+  Dims d;
+  DevState s;
+  int layout;
+  int device;
+  int sticky;          // first CUDA error seen (VBDR_ECUDA once set)
+  bool slid;           // at least one slide done
+  // host-buffer staging (allocated on first use)
+  cudaStream_t copy_stream;
+  cudaEvent_t ev_copied[2], ev_free[2];
+  uint32_t *stage[2];
+  uint64_t stage_pairs;  // capacity of one staging buffer, in pairs
+  uint32_t *d_aips;
+  float *d_out;
+  uint64_t est_cap;
+};
+
+namespace {
+
+// InitDR on every DR (Sec. 3): every field = 2^w - 1; bsLBP1 = 0; registers 0;
+// the virtual-index seed table; the pool-sum accumulators.
+__global__ void init_kernel(Dims d, DevState s, uint32_t word_init, uint32_t ktab_n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint64_t j = tid; j < d.Z; j += stride) {
+    for (uint32_t p = 0; p < d.P; ++p) s.drv[(uint64_t)p * d.Z + j] = word_init;
+    if (s.bs) s.bs[j] = 0u;
+    s.reg[j] = 0u;
+  }
+  // Alg. 3's first hash depends on the virtual index only:
+  // s1(i) = H(i, 2^32, A0), stored premixed as mix64(s1(i)).
+  const uint64_t K0 = vbk::mix64(d.A0);
+  for (uint64_t i = tid; i < ktab_n; i += stride) {
+    const uint64_t s1 = vbk::mix64(i ^ K0) >> 32;
+    s.ktab[i] = vbk::mix64(s1);
+  }
+  if (tid < 5) s.sums[tid] = 0ull;
+}
+
+int fail_cuda(vbdr *h, cudaError_t e) {
+  if (e != cudaSuccess) {
+    h->sticky = VBDR_ECUDA;
+    return VBDR_ECUDA;
+  }
+  return VBDR_OK;
+}
+
+uint32_t ktab_entries(const Dims &d) {
+  const uint32_t gmax = 1u << (d.group_rule ? d.b_min + 3 : d.b);
+  return gmax > (uint32_t)vbk::kKtabSize ? gmax : (uint32_t)vbk::kKtabSize;
+}
+
+void free_state(vbdr *h) {
+  cudaFree(h->s.drv);
+  cudaFree(h->s.bs);
+  cudaFree(h->s.reg);
+  cudaFree(h->s.ktab);
+  cudaFree(h->s.sums);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(h->stage[i]);
+    if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
+    if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
+  }
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  cudaFree(h->d_aips);
+  cudaFree(h->d_out);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vbdr_strerror(int status) {
+  switch (status) {
+    case VBDR_OK: return "ok";
+    case VBDR_EINVAL: return "invalid argument";
+    case VBDR_ENOMEM: return "out of memory";
+    case VBDR_ECUDA: return "CUDA error (handle unusable)";
+    case VBDR_ERANGE: return "size exceeds capacity";
+    case VBDR_EORDER: return "call out of order (no slide yet)";
+    case VBDR_ETIMEOUT: return "bounded device wait expired";
+    default: return "unknown status";
+  }
+}
+
+int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
+  if (!out) return VBDR_EINVAL;
+  *out = nullptr;
+  if (!cfg || cfg->reserved != 0) return VBDR_EINVAL;
+  if (cfg->k < 1 || cfg->k > 255) return VBDR_EINVAL;
+  if (cfg->layout != VBDR_GFAST && cfg->layout != VBDR_GSMALL) return VBDR_EINVAL;
+  if (cfg->group_rule > 1) return VBDR_EINVAL;
+  const uint32_t b_min = cfg->log2_g_min ? cfg->log2_g_min : cfg->log2_g;
+  if (b_min < 1 || b_min > (uint32_t)vbk::kMaxLog2G) return VBDR_EINVAL;
+  if (cfg->group_rule == 0 &&
+      (cfg->log2_g < b_min || cfg->log2_g > (uint32_t)vbk::kMaxLog2G))
+    return VBDR_EINVAL;
+  if (cfg->group_rule == 1 && b_min + 3 > 9) return VBDR_EINVAL;
+  const uint32_t b_max = cfg->group_rule ? b_min + 3 : cfg->log2_g;
+  if (cfg->num_bdr == 0 || cfg->num_bdr > (1ull << 32) ||
+      cfg->num_bdr <= (1ull << b_max))
+    return VBDR_EINVAL;
+
+  vbdr *h = new (std::nothrow) vbdr();
+  if (!h) return VBDR_ENOMEM;
+  std::memset(h, 0, sizeof(*h));
+  Dims &d = h->d;
+  d.Z = cfg->num_bdr;
+  d.zmul = d.Z == (1ull << 32) ? 0u : (uint32_t)d.Z;
+  d.k = cfg->k;
+  d.w = 0;
+  while ((1u << d.w) < cfg->k + 1) ++d.w;
+  d.F = 32 / d.w;
+  d.R = 32 - b_min;
+  d.P = (d.R + d.F - 1) / d.F;
+  d.b = cfg->group_rule ? b_min : cfg->log2_g;
+  d.b_min = b_min;
+  d.group_rule = cfg->group_rule;
+  d.A0 = cfg->seed;
+  d.A1 = vbk::mix64(cfg->seed + 0x9e3779b97f4a7c15ULL);
+  d.K1 = vbk::mix64(d.A1);
+  h->layout = (int)cfg->layout;
+  cudaGetDevice(&h->device);
+
+  uint32_t word_init = 0;
+  for (uint32_t f = 0; f < d.F; ++f) word_init |= ((1u << d.w) - 1u) << (f * d.w);
+
+  const uint32_t kn = ktab_entries(d);
+  cudaError_t e = cudaSuccess;
+  e = cudaMalloc(&h->s.drv, (size_t)d.P * d.Z * sizeof(uint32_t));
+  if (e == cudaSuccess && h->layout == VBDR_GFAST)
+    e = cudaMalloc(&h->s.bs, (size_t)d.Z * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->s.reg, (size_t)d.Z);
+  if (e == cudaSuccess) e = cudaMalloc(&h->s.ktab, (size_t)kn * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->s.sums, 8 * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_state(h);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? VBDR_ENOMEM : VBDR_ECUDA;
+  }
+  init_kernel<<<1024, 256>>>(d, h->s, word_init, kn);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_state(h);
+    delete h;
+    return VBDR_ECUDA;
+  }
+  *out = h;
+  return VBDR_OK;
+}
+
+int vbdr_destroy(vbdr_t h) {
+  if (!h) return VBDR_OK;
+  cudaDeviceSynchronize();
+  free_state(h);
+  delete h;
+  return VBDR_OK;
+}
+
+int vbdr_get_dims(vbdr_t h, uint32_t *R, uint32_t *w, uint32_t *words) {
+  if (!h) return VBDR_EINVAL;
+  if (R) *R = h->d.R;
+  if (w) *w = h->d.w;
+  if (words) *words = h->d.P;
+  return VBDR_OK;
+}
+
+int vbdr_scan_slice(vbdr_t h, const uint32_t *d_pairs, uint64_t n, void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (n == 0) return VBDR_OK;
+  if (!d_pairs || ((uintptr_t)d_pairs & 15u)) return VBDR_EINVAL;
+  return fail_cuda(h, vbk::launch_scan(h->d, h->s, h->layout == VBDR_GFAST,
+                                        d_pairs, n, (cudaStream_t)stream));
+}
+
+int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n, void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (n == 0) return VBDR_OK;
+  if (!h_pairs) return VBDR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (!h->stage[0]) {
+    const uint64_t cap = 8ull << 20;  // 8M pairs (64 MiB) per staging buffer
+    for (int i = 0; i < 2; ++i) {
+      e = cudaMalloc(&h->stage[i], cap * 8);
+      if (e != cudaSuccess) { cudaGetLastError(); return VBDR_ENOMEM; }
+      if (cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming) != cudaSuccess)
+        return fail_cuda(h, cudaErrorUnknown);
+    }
+    if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail_cuda(h, cudaErrorUnknown);
+    h->stage_pairs = cap;
+    // both buffers start free
+    for (int i = 0; i < 2; ++i) {
+      e = cudaEventRecord(h->ev_free[i], h->copy_stream);
+      if (e != cudaSuccess) return fail_cuda(h, e);
+    }
+  }
+  // The copy stream must not start before earlier work on the caller's
+  // stream that this call depends on: chain it once at the start.
+  cudaEvent_t start_ev = h->ev_copied[0];
+  e = cudaEventRecord(start_ev, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, start_ev, 0);
+  if (e != cudaSuccess) return fail_cuda(h, e);
+  uint64_t done = 0;
+  int buf = 0;
+  while (done < n) {
+    uint64_t cnt = n - done;
+    if (cnt > h->stage_pairs) cnt = h->stage_pairs;
+    e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[buf], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->stage[buf], h_pairs + 2 * done, cnt * 8,
+                          cudaMemcpyHostToDevice, h->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[buf], h->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_copied[buf], 0);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    e = vbk::launch_scan(h->d, h->s, h->layout == VBDR_GFAST, h->stage[buf], cnt, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_free[buf], st);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    done += cnt;
+    buf ^= 1;
+  }
+  return VBDR_OK;
+}
+
+int vbdr_slide(vbdr_t h, void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  int rc = fail_cuda(h, vbk::launch_slide(h->d, h->s, h->layout == VBDR_GFAST,
+                                           (cudaStream_t)stream));
+  if (rc == VBDR_OK) h->slid = true;
+  return rc;
+}
+
+int vbdr_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n, float *d_out,
+                  void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!h->slid) return VBDR_EORDER;
+  if (n == 0) return VBDR_OK;
+  if (!d_aips || !d_out || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_out & 3u))
+    return VBDR_EINVAL;
+  return fail_cuda(h, vbk::launch_estimate(h->d, h->s, d_aips, n, d_out,
+                                            (cudaStream_t)stream));
+}
+
+int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n, float *h_out,
+                       void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!h->slid) return VBDR_EORDER;
+  if (n == 0) return VBDR_OK;
+  if (!h_aips || !h_out) return VBDR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (n > h->est_cap) {
+    // wait until earlier estimates that use the old buffers are done
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    cudaFree(h->d_aips);
+    cudaFree(h->d_out);
+    h->d_aips = nullptr;
+    h->d_out = nullptr;
+    h->est_cap = 0;
+    if (cudaMalloc(&h->d_aips, n * 4) != cudaSuccess ||
+        cudaMalloc(&h->d_out, n * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return VBDR_ENOMEM;
+    }
+    h->est_cap = n;
+  }
+  e = cudaMemcpyAsync(h->d_aips, h_aips, n * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = vbk::launch_estimate(h->d, h->s, h->d_aips, n, h->d_out, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, h->d_out, n * 4, cudaMemcpyDeviceToHost, st);
+  return fail_cuda(h, e);
+}
+
+int vbdr_copy_state(vbdr_t h, uint8_t *h_dr, uint32_t *h_bs, uint8_t *h_reg,
+                    void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Dims &d = h->d;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail_cuda(h, e);
+  if (h_dr) {
+    std::vector<uint32_t> words;
+    try {
+      words.resize((size_t)d.P * d.Z);
+    } catch (...) {
+      return VBDR_ENOMEM;
+    }
+    e = cudaMemcpy(words.data(), h->s.drv, words.size() * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    const uint32_t fm = (1u << d.w) - 1u;
+    for (uint64_t j = 0; j < d.Z; ++j)
+      for (uint32_t r = 1; r <= d.R; ++r) {
+        const uint32_t p = (r - 1) / d.F, f = (r - 1) % d.F;
+        h_dr[j * d.R + (r - 1)] = (uint8_t)((words[(size_t)p * d.Z + j] >> (f * d.w)) & fm);
+      }
+  }
+  if (h_bs) {
+    if (h->s.bs)
+      e = cudaMemcpy(h_bs, h->s.bs, d.Z * 4, cudaMemcpyDeviceToHost);
+    else
+      std::memset(h_bs, 0, d.Z * 4);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+  }
+  if (h_reg) {
+    e = cudaMemcpy(h_reg, h->s.reg, d.Z, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+  }
+  return VBDR_OK;
+}
+
+int vbdr_copy_pool_sums(vbdr_t h, uint64_t *S_Z, uint64_t *V_Z, void *stream) {
+  if (!h || !S_Z || !V_Z) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  unsigned long long v[2];
+  cudaError_t e = cudaMemcpyAsync(v, h->s.sums, sizeof(v), cudaMemcpyDeviceToHost,
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fail_cuda(h, e);
+  *S_Z = v[0];
+  *V_Z = v[1];
+  return VBDR_OK;
+}
+
+}  // extern "C"

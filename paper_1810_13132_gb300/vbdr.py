@@ -1,0 +1,216 @@
+"""Python binding of the VBDR C ABI (include/vbdr.h) -- argument marshalling only.
+
+Every step of the method runs in the CUDA library libvbdr.so; this module only
+passes device pointers (``torch.Tensor.data_ptr()``) and the current CUDA
+stream.  There is no CPU fallback: without the library or a GPU every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+VBDR_GFAST, VBDR_GSMALL = 0, 1
+LAYOUTS = {"gfast": VBDR_GFAST, "gsmall": VBDR_GSMALL}
+
+STATUS = {0: "VBDR_OK", -1: "VBDR_EINVAL", -2: "VBDR_ENOMEM", -3: "VBDR_ECUDA",
+          -4: "VBDR_ERANGE", -5: "VBDR_EORDER", -6: "VBDR_ETIMEOUT"}
+
+
+class VbdrError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        self.code = code
+        super().__init__(f"{fn} failed: {STATUS.get(code, code)} ({_strerror(code)})")
+
+
+class vbdr_config(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("log2_g", ctypes.c_uint32),
+                ("log2_g_min", ctypes.c_uint32), ("group_rule", ctypes.c_uint32),
+                ("layout", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("num_bdr", ctypes.c_uint64), ("seed", ctypes.c_uint64)]
+
+
+# Every symbol include/vbdr.h declares, with (restype, argtypes).
+_VP, _U32, _U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+_SIGS = {
+    "vbdr_create": (ctypes.c_int, [ctypes.POINTER(vbdr_config), ctypes.POINTER(_VP)]),
+    "vbdr_destroy": (ctypes.c_int, [_VP]),
+    "vbdr_scan_slice": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
+    "vbdr_scan_slice_host": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
+    "vbdr_slide": (ctypes.c_int, [_VP, _VP]),
+    "vbdr_estimate": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
+    "vbdr_estimate_host": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
+    "vbdr_get_dims": (ctypes.c_int, [_VP, ctypes.POINTER(_U32), ctypes.POINTER(_U32),
+                                     ctypes.POINTER(_U32)]),
+    "vbdr_copy_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "vbdr_copy_pool_sums": (ctypes.c_int, [_VP, ctypes.POINTER(_U64),
+                                           ctypes.POINTER(_U64), _VP]),
+    "vbdr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libvbdr.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+def _strerror(code: int) -> str:
+    try:
+        return load(build_if_missing=False).vbdr_strerror(code).decode()
+    except Exception:
+        return "?"
+
+
+def _check(fn: str, rc: int) -> None:
+    if rc != 0:
+        raise VbdrError(fn, rc)
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+@dataclass
+class Config:
+    k: int
+    num_bdr: int
+    log2_g: int
+    seed: int = 0x9E3779B97F4A7C15
+    layout: str = "gfast"
+    log2_g_min: int = 0
+    group_rule: int = 0
+
+    def to_c(self) -> vbdr_config:
+        return vbdr_config(self.k, self.log2_g, self.log2_g_min, self.group_rule,
+                           LAYOUTS[self.layout], 0, self.num_bdr, self.seed)
+
+
+class Vbdr:
+    """One VBDR instance with device-resident state (see include/vbdr.h).
+
+    ``scan(pairs)`` takes an (n, 2) uint32/int32 CUDA tensor of (aip, bip),
+    ``slide()`` closes the slice, ``estimate(aips)`` returns float32
+    estimates on the device.  Calls run on the current torch CUDA stream.
+    """
+
+    def __init__(self, cfg: Config):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("VBDR needs a CUDA GPU; no CPU fallback exists")
+        torch.cuda.init()
+        self.cfg = cfg
+        self._L = load()
+        h = ctypes.c_void_p()
+        c = cfg.to_c()
+        _check("vbdr_create", self._L.vbdr_create(ctypes.byref(c), ctypes.byref(h)))
+        self._h = h
+        R, w, P = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check("vbdr_get_dims", self._L.vbdr_get_dims(h, ctypes.byref(R), ctypes.byref(w),
+                                                      ctypes.byref(P)))
+        self.R, self.w, self.words = R.value, w.value, P.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._L.vbdr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the hot path ----------------------------------------------------------
+    def scan(self, pairs, stream=None) -> None:
+        import torch
+        assert pairs.is_cuda and pairs.is_contiguous()
+        assert pairs.dtype in (torch.int32, torch.uint32)
+        n = pairs.numel() // 2
+        _check("vbdr_scan_slice", self._L.vbdr_scan_slice(
+            self._h, pairs.data_ptr() if n else None, n, _stream_ptr(stream)))
+
+    def scan_host(self, pairs: np.ndarray, stream=None) -> None:
+        """Scan pairs held in host memory (numpy or pinned torch CPU tensor)."""
+        ptr, n = _host_ptr(pairs, 2)
+        _check("vbdr_scan_slice_host", self._L.vbdr_scan_slice_host(
+            self._h, ptr, n, _stream_ptr(stream)))
+
+    def slide(self, stream=None) -> None:
+        _check("vbdr_slide", self._L.vbdr_slide(self._h, _stream_ptr(stream)))
+
+    def estimate(self, aips, out=None, stream=None):
+        import torch
+        assert aips.is_cuda and aips.is_contiguous()
+        n = aips.numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=aips.device)
+        _check("vbdr_estimate", self._L.vbdr_estimate(
+            self._h, aips.data_ptr() if n else None, n, out.data_ptr() if n else None,
+            _stream_ptr(stream)))
+        return out
+
+    def estimate_host(self, aips, out, stream=None) -> None:
+        pa, n = _host_ptr(aips, 1)
+        po, n2 = _host_ptr(out, 1)
+        assert n == n2
+        _check("vbdr_estimate_host", self._L.vbdr_estimate_host(
+            self._h, pa, n, po, _stream_ptr(stream)))
+
+    # -- inspection --------------------------------------------------------------
+    def state(self, stream=None) -> dict:
+        Z = self.cfg.num_bdr
+        dr = np.empty((Z, self.R), dtype=np.uint8)
+        bs = np.empty(Z, dtype=np.uint32)
+        reg = np.empty(Z, dtype=np.uint8)
+        _check("vbdr_copy_state", self._L.vbdr_copy_state(
+            self._h, dr.ctypes.data, bs.ctypes.data, reg.ctypes.data, _stream_ptr(stream)))
+        return {"dr": dr, "bs": bs, "reg": reg}
+
+    def registers(self, stream=None) -> np.ndarray:
+        reg = np.empty(self.cfg.num_bdr, dtype=np.uint8)
+        _check("vbdr_copy_state", self._L.vbdr_copy_state(
+            self._h, None, None, reg.ctypes.data, _stream_ptr(stream)))
+        return reg
+
+    def pool_sums(self, stream=None) -> tuple[int, int]:
+        S, V = ctypes.c_uint64(), ctypes.c_uint64()
+        _check("vbdr_copy_pool_sums", self._L.vbdr_copy_pool_sums(
+            self._h, ctypes.byref(S), ctypes.byref(V), _stream_ptr(stream)))
+        return S.value, V.value
+
+
+def _host_ptr(a, width: int):
+    """(pointer, element count / width) of a C-contiguous host array."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return (a.ctypes.data if a.size else None), a.size // width
+    assert not a.is_cuda and a.is_contiguous()
+    return (a.data_ptr() if a.numel() else None), a.numel() // width

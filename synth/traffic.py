@@ -118,13 +118,15 @@ class ZipfTraffic:
         out[:, 0] = self.aips[host]
         out[:, 1] = self.pool[self.pool_off[host] + j]
         if self.repeat_frac > 0 and n > 1:
-            n_rep = int(n * self.repeat_frac)
-            pos = self.rng.choice(np.arange(1, n), size=min(n_rep, n - 1),
-                                  replace=False)
-            half = pos.size // 2
-            adj = np.sort(pos[:half])
+            # each position i >= 1 becomes a repeat with probability
+            # repeat_frac, half of them of the previous pair (bursts), half
+            # of a uniformly random earlier pair
+            u = self.rng.random(n)
+            u[0] = 1.0
+            pos = np.nonzero(u < self.repeat_frac)[0]
+            adj = pos[u[pos] < self.repeat_frac / 2]
+            far = pos[u[pos] >= self.repeat_frac / 2]
             out[adj] = out[adj - 1]  # bursts: copy the previous pair
-            far = pos[half:]
             src = (self.rng.random(far.size) * far).astype(np.int64)
             out[far] = out[src]      # copies of a random earlier pair
         return out
