@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of include/vbdr.h: argument checks, device state
 // ownership, host-buffer staging, and the state-initialisation kernel.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -11,10 +12,12 @@
 
 using vbk::DevState;
 using vbk::Dims;
+using vbk::EstConst;
 
 struct vbdr {
   Dims d;
   DevState s;
+  vbk::EstConst est;
   int layout;
   int device;
   int sticky;          // first CUDA error seen (VBDR_ECUDA once set)
@@ -36,19 +39,40 @@ namespace {
 __global__ void init_kernel(Dims d, DevState s, uint32_t word_init, uint32_t ktab_n) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (uint64_t j = tid; j < d.Z; j += stride) {
-    for (uint32_t p = 0; p < d.P; ++p) s.drv[(uint64_t)p * d.Z + j] = word_init;
-    if (s.bs) s.bs[j] = 0u;
-    s.reg[j] = 0u;
+  for (uint64_t j = tid; j < d.Zs; j += stride) {
+    for (uint32_t p = 0; p < d.P; ++p) s.drv[(uint64_t)p * d.Zs + j] = word_init;
+    if (j < d.Z) {
+      if (s.bs) s.bs[j] = 0u;
+      s.reg[j] = 0u;
+    }
   }
   // Alg. 3's first hash depends on the virtual index only:
   // s1(i) = H(i, 2^32, A0), stored premixed as mix64(s1(i)).
   const uint64_t K0 = vbk::mix64(d.A0);
   for (uint64_t i = tid; i < ktab_n; i += stride) {
     const uint64_t s1 = vbk::mix64(i ^ K0) >> 32;
-    s.ktab[i] = vbk::mix64(s1);
+    s.ktab[i] = vbk::make_kent(vbk::mix64(s1));
   }
   if (tid < 5) s.sums[tid] = 0ull;
+}
+
+// HyperLogLog bias constant alpha_m (Flajolet et al. 2007).
+double hll_alpha(double m) {
+  if (m == 16.0) return 0.673;
+  if (m == 32.0) return 0.697;
+  if (m == 64.0) return 0.709;
+  return 0.7213 / (1.0 + 1.079 / m);
+}
+
+void fill_est_const(const Dims &d, EstConst *c) {
+  const double Z = (double)d.Z;
+  for (int b = 0; b <= vbk::kMaxLog2G; ++b) {
+    const double g = (double)(1u << b);
+    c->amm[b] = hll_alpha(g) * g * g;
+    c->kz[b] = Z * g / (Z - g);
+    c->lng[b] = std::log(g);
+  }
+  c->amm_Z = hll_alpha(Z) * Z * Z;
 }
 
 int fail_cuda(vbdr *h, cudaError_t e) {
@@ -69,6 +93,7 @@ void free_state(vbdr *h) {
   cudaFree(h->s.bs);
   cudaFree(h->s.reg);
   cudaFree(h->s.ktab);
+  cudaFree(h->s.lnv);
   cudaFree(h->s.sums);
   for (int i = 0; i < 2; ++i) {
     cudaFree(h->stage[i]);
@@ -120,6 +145,7 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   std::memset(h, 0, sizeof(*h));
   Dims &d = h->d;
   d.Z = cfg->num_bdr;
+  d.Zs = (d.Z + 3) & ~3ull;
   d.zmul = d.Z == (1ull << 32) ? 0u : (uint32_t)d.Z;
   d.k = cfg->k;
   d.w = 0;
@@ -132,7 +158,7 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   d.group_rule = cfg->group_rule;
   d.A0 = cfg->seed;
   d.A1 = vbk::mix64(cfg->seed + 0x9e3779b97f4a7c15ULL);
-  d.K1 = vbk::mix64(d.A1);
+  d.K1 = vbk::make_kent(vbk::mix64(d.A1));
   h->layout = (int)cfg->layout;
   cudaGetDevice(&h->device);
 
@@ -141,12 +167,20 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
 
   const uint32_t kn = ktab_entries(d);
   cudaError_t e = cudaSuccess;
-  e = cudaMalloc(&h->s.drv, (size_t)d.P * d.Z * sizeof(uint32_t));
+  e = cudaMalloc(&h->s.drv, (size_t)d.P * d.Zs * sizeof(uint32_t));
   if (e == cudaSuccess && h->layout == VBDR_GFAST)
     e = cudaMalloc(&h->s.bs, (size_t)d.Z * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.reg, (size_t)d.Z);
-  if (e == cudaSuccess) e = cudaMalloc(&h->s.ktab, (size_t)kn * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->s.ktab, (size_t)kn * sizeof(vbk::KEnt));
+  if (e == cudaSuccess) e = cudaMalloc(&h->s.lnv, vbk::kLnTab * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.sums, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    double lnv[vbk::kLnTab];
+    lnv[0] = 0.0;
+    for (int v = 1; v < vbk::kLnTab; ++v) lnv[v] = std::log((double)v);
+    e = cudaMemcpy(h->s.lnv, lnv, sizeof(lnv), cudaMemcpyHostToDevice);
+  }
+  fill_est_const(d, &h->est);
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_state(h);
@@ -259,7 +293,7 @@ int vbdr_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n, float *d_out,
   if (n == 0) return VBDR_OK;
   if (!d_aips || !d_out || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_out & 3u))
     return VBDR_EINVAL;
-  return fail_cuda(h, vbk::launch_estimate(h->d, h->s, d_aips, n, d_out,
+  return fail_cuda(h, vbk::launch_estimate(h->d, h->s, h->est, d_aips, n, d_out,
                                             (cudaStream_t)stream));
 }
 
@@ -289,7 +323,7 @@ int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n, float *h_ou
     h->est_cap = n;
   }
   e = cudaMemcpyAsync(h->d_aips, h_aips, n * 4, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = vbk::launch_estimate(h->d, h->s, h->d_aips, n, h->d_out, st);
+  if (e == cudaSuccess) e = vbk::launch_estimate(h->d, h->s, h->est, h->d_aips, n, h->d_out, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, h->d_out, n * 4, cudaMemcpyDeviceToHost, st);
   return fail_cuda(h, e);
 }
@@ -305,7 +339,7 @@ int vbdr_copy_state(vbdr_t h, uint8_t *h_dr, uint32_t *h_bs, uint8_t *h_reg,
   if (h_dr) {
     std::vector<uint32_t> words;
     try {
-      words.resize((size_t)d.P * d.Z);
+      words.resize((size_t)d.P * d.Zs);
     } catch (...) {
       return VBDR_ENOMEM;
     }
@@ -315,7 +349,7 @@ int vbdr_copy_state(vbdr_t h, uint8_t *h_dr, uint32_t *h_bs, uint8_t *h_reg,
     for (uint64_t j = 0; j < d.Z; ++j)
       for (uint32_t r = 1; r <= d.R; ++r) {
         const uint32_t p = (r - 1) / d.F, f = (r - 1) % d.F;
-        h_dr[j * d.R + (r - 1)] = (uint8_t)((words[(size_t)p * d.Z + j] >> (f * d.w)) & fm);
+        h_dr[j * d.R + (r - 1)] = (uint8_t)((words[(size_t)p * d.Zs + j] >> (f * d.w)) & fm);
       }
   }
   if (h_bs) {

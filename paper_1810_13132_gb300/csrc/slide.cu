@@ -10,9 +10,16 @@
 // for its noise term.  Exact 64-bit integer sums: the result does not depend
 // on the reduction order.
 //
-// One thread per BDR, grid-stride; each DRV plane is a coalesced 4-byte
-// stream.  The saturating increment is SWAR: a field is incremented unless
-// all its w bits are set, so no carry ever crosses a field.
+// Streaming layout: each thread owns 4 consecutive BDRs and moves them with
+// 16-byte accesses -- one uint4 per DRV plane, one uint4 of bsLBP1, one
+// 4-byte store of the 4 registers -- so a warp moves 512 contiguous bytes
+// per plane.  The field arithmetic is SWAR on whole words:
+//   saturating +1 : a field is incremented unless all its w bits are set,
+//                   so no carry crosses a field;
+//   active test   : even and odd fields are split apart so that every field
+//                   has a w-bit zero gap above it; OR-ing a guard bit into the
+//                   gap and subtracting k from every field leaves the guard
+//                   set exactly for the fields with DR >= k (inactive).
 #include "vbdr_internal.cuh"
 
 namespace vbk {
@@ -22,84 +29,152 @@ constexpr int kSlideThreads = 256;
 
 template <int W>
 struct Fields {
-  static constexpr uint32_t F = 32 / W;                       // fields per word
-  static constexpr uint32_t FM = (1u << W) - 1u;              // one field
-  static constexpr uint32_t PMAX = (31 + F - 1) / F;          // R <= 31
-  static constexpr uint32_t lsb_mask() {
+  static constexpr uint32_t F = 32 / W;               // fields per word
+  static constexpr uint32_t FM = (1u << W) - 1u;      // one field
+  static constexpr uint32_t PMAX = (31 + F - 1) / F;  // planes for R <= 31
+  static constexpr uint32_t lsb(uint32_t parity) {    // LSB of fields f%2==parity
     uint32_t m = 0;
-    for (uint32_t f = 0; f < F; ++f) m |= 1u << (f * W);
+    for (uint32_t f = parity; f < F; f += 2) m |= 1u << (f * W);
     return m;
   }
+  static constexpr uint32_t LSB = lsb(0) | lsb(1);
+  static constexpr uint32_t EVEN = lsb(0) * FM;       // all bits of even fields
 };
 
-// Saturating +1 of every field of one word (fields past R hold DR_MAX and
-// stay there).
-template <int W>
-__device__ __forceinline__ uint32_t sat_inc(uint32_t x) {
-  constexpr uint32_t L = Fields<W>::lsb_mask();
-  uint32_t all = x;
-#pragma unroll
-  for (int sft = 1; sft < W; ++sft) all &= x >> sft;
-  return x + (L & ~all);
+// x >> s computed as the high word of x * 2^(32-s): the multiply pipe is
+// otherwise idle here while the logic pipe carries the masks.
+template <int S>
+__device__ __forceinline__ uint32_t shr(uint32_t x) {
+  static_assert(S >= 1 && S <= 31, "shift");
+  return __umulhi(x, 1u << (32 - S));
 }
 
-// Largest r in 1..R with DR[r] < k, else 0 (Alg. 2).
+// Saturating +1 of every field of one word.
 template <int W>
-__device__ __forceinline__ uint32_t register_of(const uint32_t *words,
-                                                uint32_t P, uint32_t R,
-                                                uint32_t k) {
-  constexpr uint32_t F = Fields<W>::F;
+__device__ __forceinline__ uint32_t sat_inc(uint32_t x) {
+  uint32_t all = x;
+  if constexpr (W >= 2) all &= shr<1>(x);
+  if constexpr (W >= 3) all &= shr<2>(x);
+  if constexpr (W >= 4) all &= shr<3>(x);
+  if constexpr (W >= 5) all &= shr<4>(x);
+  if constexpr (W >= 6) all &= shr<5>(x);
+  if constexpr (W >= 7) all &= shr<6>(x);
+  if constexpr (W >= 8) all &= shr<7>(x);
+  return x + (Fields<W>::LSB & ~all);
+}
+
+// Bit f*W set for every field f of x with value < k (an active DR).
+template <int W>
+__device__ __forceinline__ uint32_t active_fields(uint32_t x, uint32_t krep_even) {
+  constexpr uint32_t EVEN = Fields<W>::EVEN;
+  constexpr uint32_t GUARD = Fields<W>::lsb(0) << W;  // bit just above each even field
+  const uint32_t e = x & EVEN;
+  const uint32_t o = shr<W>(x) & EVEN;
+  const uint32_t te = (e | GUARD) - krep_even;  // guard survives iff field >= k
+  const uint32_t to = (o | GUARD) - krep_even;
+  const uint32_t ae = ~te & GUARD;              // active even fields, at f*W + W
+  const uint32_t ao = ~to & GUARD;              // active odd fields, at f*W
+  // an odd field count leaves a phantom field above the last one: drop it
+  return (shr<W>(ae) | ao) & Fields<W>::LSB;
+}
+
+// Alg. 2 on one BDR whose P words are w[0..P): the largest LBP1 r in 1..R
+// with DR[r] < k, else 0.  Fields past R hold 2^w - 1 >= k: never active.
+template <int W, int P>
+__device__ __forceinline__ uint32_t register_of(const uint32_t (&w)[P], uint32_t krep_even) {
   uint32_t reg = 0;
 #pragma unroll
-  for (uint32_t p = 0; p < Fields<W>::PMAX; ++p) {
-    if (p < P) {
-#pragma unroll
-      for (uint32_t f = 0; f < F; ++f) {
-        const uint32_t r = p * F + f + 1;
-        const uint32_t dr = (words[p] >> (f * W)) & Fields<W>::FM;
-        if (r <= R && dr < k) reg = r;
-      }
-    }
+  for (int p = 0; p < P; ++p) {
+    const uint32_t a = active_fields<W>(w[p], krep_even);
+    if (a) reg = (uint32_t)p * Fields<W>::F + (31u - (uint32_t)__clz(a)) / W + 1u;
   }
   return reg;
 }
 
-template <int W, bool GFAST>
+// gfast: zero the DR of the highest set bit of bsLBP1 (Alg. 6).
+template <int W, int PMAX>
+__device__ __forceinline__ void set_dr_of_top_bit(uint32_t (&w)[PMAX], uint32_t bsv) {
+  if (bsv) {
+    const uint32_t r0 = 31u - (uint32_t)__clz(bsv);  // LBP1 - 1
+    const uint32_t pw = r0 / Fields<W>::F;
+    const uint32_t clear = ~(Fields<W>::FM << ((r0 % Fields<W>::F) * W));
+#pragma unroll
+    for (int p = 0; p < PMAX; ++p)
+      if ((uint32_t)p == pw) w[p] &= clear;
+  }
+}
+
+template <int W, int P, bool GFAST>
+__device__ __forceinline__ uint32_t slide_one(uint32_t (&w)[P], uint32_t bsv,
+                                              uint32_t krep_even) {
+  if constexpr (GFAST) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) w[p] = sat_inc<W>(w[p]);
+    set_dr_of_top_bit<W, P>(w, bsv);
+    return register_of<W, P>(w, krep_even);
+  } else {
+    const uint32_t reg = register_of<W, P>(w, krep_even);
+#pragma unroll
+    for (int p = 0; p < P; ++p) w[p] = sat_inc<W>(w[p]);
+    return reg;
+  }
+}
+
+__device__ __forceinline__ uint32_t comp(const uint4 &v, int c) {
+  return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void set_comp(uint4 &v, int c, uint32_t x) {
+  if (c == 0) v.x = x; else if (c == 1) v.y = x; else if (c == 2) v.z = x; else v.w = x;
+}
+
+template <int W, int P, bool GFAST>
 __global__ void __launch_bounds__(kSlideThreads)
-    slide_kernel(Dims d, DevState s) {
-  constexpr uint32_t PMAX = Fields<W>::PMAX;
-  constexpr uint32_t F = Fields<W>::F;
+    slide_kernel(Dims d, DevState s, uint32_t krep_even) {
   unsigned long long S = 0, V = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < d.Z;
-       j += stride) {
-    uint32_t w0[PMAX], w1[PMAX];
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t quads = d.Z >> 2;
+  for (uint64_t q = tid; q < quads; q += stride) {
+    const uint64_t j = q << 2;
+    uint4 v[P];
 #pragma unroll
-    for (uint32_t p = 0; p < PMAX; ++p)
-      w0[p] = (p < d.P) ? __ldcs(s.drv + (uint64_t)p * d.Z + j) : 0u;
-    uint32_t reg;
-    if constexpr (GFAST) {
+    for (int p = 0; p < P; ++p)
+      v[p] = __ldcs(reinterpret_cast<const uint4 *>(s.drv + (uint64_t)p * d.Zs + j));
+    uint4 bsq = make_uint4(0, 0, 0, 0);
+    if constexpr (GFAST) bsq = __ldcs(reinterpret_cast<const uint4 *>(s.bs + j));
+    uint32_t regs = 0;
 #pragma unroll
-      for (uint32_t p = 0; p < PMAX; ++p) w1[p] = sat_inc<W>(w0[p]);
-      const uint32_t bsv = __ldcs(s.bs + j);
-      if (bsv) {
-        const uint32_t r0 = 31u - (uint32_t)__clz(bsv);  // LBP1 - 1 of the top bit
-        const uint32_t pw = r0 / F;
-        const uint32_t clear = ~(Fields<W>::FM << ((r0 % F) * W));
+    for (int c = 0; c < 4; ++c) {
+      uint32_t w[P];
 #pragma unroll
-        for (uint32_t p = 0; p < PMAX; ++p)
-          if (p == pw) w1[p] &= clear;
-        __stcs(s.bs + j, 0u);
-      }
-      reg = register_of<W>(w1, d.P, d.R, d.k);
-    } else {
-      reg = register_of<W>(w0, d.P, d.R, d.k);
+      for (int p = 0; p < P; ++p) w[p] = comp(v[p], c);
+      const uint32_t reg = slide_one<W, P, GFAST>(w, comp(bsq, c), krep_even);
 #pragma unroll
-      for (uint32_t p = 0; p < PMAX; ++p) w1[p] = sat_inc<W>(w0[p]);
+      for (int p = 0; p < P; ++p) set_comp(v[p], c, w[p]);
+      regs |= reg << (8 * c);
+      S += 1ull << (32u - reg);
+      V += (reg == 0u);
     }
 #pragma unroll
-    for (uint32_t p = 0; p < PMAX; ++p)
-      if (p < d.P && w1[p] != w0[p]) __stcs(s.drv + (uint64_t)p * d.Z + j, w1[p]);
+    for (int p = 0; p < P; ++p)
+      __stcs(reinterpret_cast<uint4 *>(s.drv + (uint64_t)p * d.Zs + j), v[p]);
+    if constexpr (GFAST) {
+      if (bsq.x | bsq.y | bsq.z | bsq.w)
+        __stcs(reinterpret_cast<uint4 *>(s.bs + j), make_uint4(0, 0, 0, 0));
+    }
+    __stcs(reinterpret_cast<uint32_t *>(s.reg + j), regs);
+  }
+  // the last Z mod 4 BDRs, one thread each
+  if (tid < (d.Z & 3u)) {
+    const uint64_t j = (quads << 2) + tid;
+    uint32_t w[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) w[p] = s.drv[(uint64_t)p * d.Zs + j];
+    const uint32_t bsv = GFAST ? s.bs[j] : 0u;
+    const uint32_t reg = slide_one<W, P, GFAST>(w, bsv, krep_even);
+#pragma unroll
+    for (int p = 0; p < P; ++p) s.drv[(uint64_t)p * d.Zs + j] = w[p];
+    if (GFAST && bsv) s.bs[j] = 0u;
     s.reg[j] = (uint8_t)reg;
     S += 1ull << (32u - reg);
     V += (reg == 0u);
@@ -131,40 +206,58 @@ __global__ void __launch_bounds__(kSlideThreads)
   }
 }
 
-template <int W>
-cudaError_t launch_slide_t(const Dims &d, const DevState &s, bool gfast,
-                           cudaStream_t st) {
+template <int W, int P>
+cudaError_t launch_slide_t(const Dims &d, const DevState &s, bool gfast, cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (gfast)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slide_kernel<W, true>, kSlideThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slide_kernel<W, P, true>, kSlideThreads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slide_kernel<W, false>, kSlideThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slide_kernel<W, P, false>, kSlideThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  const uint64_t want = (d.Z + kSlideThreads - 1) / kSlideThreads;
+  const uint64_t want = ((d.Z >> 2) + kSlideThreads - 1) / kSlideThreads;
   uint64_t grid = (uint64_t)sms * per_sm;
-  if (want < grid) grid = want;
+  if (want < grid) grid = want ? want : 1;
+  // k replicated into every even field (the subtrahend of the active test)
+  uint32_t krep = 0;
+  for (uint32_t f = 0; f < Fields<W>::F; f += 2) krep |= d.k << (f * W);
   if (gfast)
-    slide_kernel<W, true><<<(unsigned)grid, kSlideThreads, 0, st>>>(d, s);
+    slide_kernel<W, P, true><<<(unsigned)grid, kSlideThreads, 0, st>>>(d, s, krep);
   else
-    slide_kernel<W, false><<<(unsigned)grid, kSlideThreads, 0, st>>>(d, s);
+    slide_kernel<W, P, false><<<(unsigned)grid, kSlideThreads, 0, st>>>(d, s, krep);
   return cudaGetLastError();
+}
+
+// P = ceil(R / floor(32 / W)) DRV words per BDR, R = 32 - b_min in 16..31.
+template <int W>
+cudaError_t launch_slide_w(const Dims &d, const DevState &s, bool gfast, cudaStream_t st) {
+  constexpr int F = 32 / W;
+  constexpr int PLO = (16 + F - 1) / F, PHI = (31 + F - 1) / F;
+  switch (d.P) {
+#define VBK_SLIDE_P(PP) \
+    case PP: if constexpr (PP >= PLO && PP <= PHI) return launch_slide_t<W, PP>(d, s, gfast, st); break;
+    VBK_SLIDE_P(1) VBK_SLIDE_P(2) VBK_SLIDE_P(3) VBK_SLIDE_P(4) VBK_SLIDE_P(5) VBK_SLIDE_P(6)
+    VBK_SLIDE_P(7) VBK_SLIDE_P(8) VBK_SLIDE_P(9) VBK_SLIDE_P(10) VBK_SLIDE_P(11) VBK_SLIDE_P(12)
+    VBK_SLIDE_P(13) VBK_SLIDE_P(14) VBK_SLIDE_P(15) VBK_SLIDE_P(16) VBK_SLIDE_P(31)
+#undef VBK_SLIDE_P
+    default: break;
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t launch_slide(const Dims &d, const DevState &s, bool gfast,
-                         cudaStream_t st) {
+cudaError_t launch_slide(const Dims &d, const DevState &s, bool gfast, cudaStream_t st) {
   switch (d.w) {
-    case 1: return launch_slide_t<1>(d, s, gfast, st);
-    case 2: return launch_slide_t<2>(d, s, gfast, st);
-    case 3: return launch_slide_t<3>(d, s, gfast, st);
-    case 4: return launch_slide_t<4>(d, s, gfast, st);
-    case 5: return launch_slide_t<5>(d, s, gfast, st);
-    case 6: return launch_slide_t<6>(d, s, gfast, st);
-    case 7: return launch_slide_t<7>(d, s, gfast, st);
-    case 8: return launch_slide_t<8>(d, s, gfast, st);
+    case 1: return launch_slide_w<1>(d, s, gfast, st);
+    case 2: return launch_slide_w<2>(d, s, gfast, st);
+    case 3: return launch_slide_w<3>(d, s, gfast, st);
+    case 4: return launch_slide_w<4>(d, s, gfast, st);
+    case 5: return launch_slide_w<5>(d, s, gfast, st);
+    case 6: return launch_slide_w<6>(d, s, gfast, st);
+    case 7: return launch_slide_w<7>(d, s, gfast, st);
+    case 8: return launch_slide_w<8>(d, s, gfast, st);
     default: return cudaErrorInvalidValue;
   }
 }

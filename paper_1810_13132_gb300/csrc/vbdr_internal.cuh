@@ -1,7 +1,9 @@
 // vbdr_internal.cuh -- device-side definitions shared by the VBDR kernels.
 //
 // Data layout in HBM (per handle, Z physical BDRs):
-//   drv   : P word planes of Z uint32 each, plane-major (drv[p * Z + j]).
+//   drv   : P word planes of Z uint32 each, plane-major (drv[p * Zs + j],
+//           Zs = Z rounded up to a multiple of 4 so every plane is 16 B
+//           aligned for vector access).
 //           Word p of BDR j packs the DRs of LBP1 values p*F+1 .. p*F+F,
 //           F = floor(32 / w) fields of w bits, field f at bits [f*w, f*w+w).
 //           Plane-major puts every BDR's first word (LBP1 1..F, which takes
@@ -10,8 +12,9 @@
 //           gsmall scan touch a quarter of the DRV footprint.
 //   bs    : Z uint32, bsLBP1 of the gfast layout (bit r-1 <-> LBP1 r).
 //   reg   : Z uint8, register of every BDR at the last slide (Alg. 2).
-//   ktab  : 512 uint64, mix64(s1(i)) for virtual index i, s1(i) = H(i,2^32,A0)
-//           (the first hash of Alg. 3, which depends only on i).
+//   ktab  : max(g_max, 512) KEnt, the premixed seed mix64(s1(i)) of virtual
+//           index i, s1(i) = H(i,2^32,A0) (the first hash of Alg. 3, which
+//           depends only on i), split as KEnt.
 //   sums  : pool sums S_Z, V_Z and the block-completion counter of the slide.
 #pragma once
 
@@ -22,6 +25,7 @@ namespace vbk {
 
 constexpr int kMaxLog2G = 16;
 constexpr int kKtabSize = 512;  // virtual indices covered by the smem table
+constexpr int kLnTab = 513;     // ln(v) tabulated for v = 0..512 (entry 0 unused)
 
 // SplitMix64 output mix (Steele, Lea & Flood 2014), used as the seeded hash
 // H(x, N, A) of Sec. 4.1:  H(x,N,A) = (hi32(mix64(x ^ mix64(A))) * N) >> 32.
@@ -31,9 +35,40 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// hi32(mix64(x ^ K)) for a 32-bit x and a premixed seed K = mix64(A).
-__device__ __forceinline__ uint32_t hash32(uint32_t x, uint64_t K) {
-  return (uint32_t)(mix64((uint64_t)x ^ K) >> 32);
+// A premixed seed K = mix64(A) split for evaluating hi32(mix64(x ^ K)) of a
+// 32-bit x in 32-bit halves: the high half of x ^ K is K's, so the terms of
+// the first xor-shift and first multiply that depend on it alone are
+// precomputed (hi1 = Khi ^ (Khi >> 30), t1 = hi1 * C1lo).
+struct KEnt {
+  uint32_t lo, hi, hi1, t1;
+};
+
+constexpr uint64_t kMixC1 = 0xbf58476d1ce4e5b9ULL, kMixC2 = 0x94d049bb133111ebULL;
+
+__host__ __device__ __forceinline__ KEnt make_kent(uint64_t K) {
+  KEnt e;
+  e.lo = (uint32_t)K;
+  e.hi = (uint32_t)(K >> 32);
+  e.hi1 = e.hi ^ (e.hi >> 30);
+  e.t1 = e.hi1 * (uint32_t)kMixC1;
+  return e;
+}
+
+// hi32(mix64(x ^ K)) -- the same value as mix64 above, in 32-bit pieces:
+//   z ^= z >> 30 ; z *= C1 ; z ^= z >> 27 ; z *= C2 ; z ^= z >> 31
+// of which only the high word of the last two steps is needed.
+__device__ __forceinline__ uint32_t hash32(uint32_t x, const KEnt &k) {
+  constexpr uint32_t C1lo = (uint32_t)kMixC1, C1hi = (uint32_t)(kMixC1 >> 32);
+  constexpr uint32_t C2lo = (uint32_t)kMixC2, C2hi = (uint32_t)(kMixC2 >> 32);
+  const uint32_t lo0 = x ^ k.lo;
+  const uint32_t lo1 = lo0 ^ __funnelshift_r(lo0, k.hi, 30);
+  const uint64_t p = (uint64_t)lo1 * C1lo;
+  const uint32_t lo2 = (uint32_t)p;
+  const uint32_t hi2 = (uint32_t)(p >> 32) + lo1 * C1hi + k.t1;
+  const uint32_t lo3 = lo2 ^ __funnelshift_r(lo2, hi2, 27);
+  const uint32_t hi3 = hi2 ^ (hi2 >> 27);
+  const uint32_t hi4 = __umulhi(lo3, C2lo) + lo3 * C2hi + hi3 * C2lo;
+  return hi4 ^ (hi4 >> 31);
 }
 
 // Multiply-shift range reduction of a 32-bit hash onto [0, Z); Z = 2^32 is
@@ -44,6 +79,7 @@ __device__ __forceinline__ uint32_t reduce32(uint32_t h, uint32_t zmul) {
 
 struct Dims {
   uint64_t Z;        // physical BDRs
+  uint64_t Zs;       // DRV plane stride in words: Z rounded up to 4 (16 B)
   uint32_t zmul;     // Z as a 32-bit multiplier (0 when Z = 2^32)
   uint32_t k;        // window in slices
   uint32_t w;        // DR width in bits
@@ -54,14 +90,26 @@ struct Dims {
   uint32_t b_min;    // smallest log2 g
   uint32_t group_rule;
   uint64_t A0, A1;   // seeds
-  uint64_t K1;       // mix64(A1): premixed seed of the bip hash
+  KEnt K1;           // mix64(A1): premixed seed of the bip hash
+};
+
+// Per-handle FP64 constants of the estimator, indexed by b = log2 g (each
+// computed on the host with the same IEEE operations, in the same order, as
+// the plain formula): amm[b] = alpha_g * g * g, kz[b] = Z * g / (Z - g),
+// lng[b] = ln g; amm_Z = alpha_Z * Z * Z for the pool.
+struct EstConst {
+  double amm[kMaxLog2G + 1];
+  double kz[kMaxLog2G + 1];
+  double lng[kMaxLog2G + 1];
+  double amm_Z;
 };
 
 struct DevState {
-  uint32_t *drv;     // [P][Z]
+  uint32_t *drv;     // [P][Zs]
   uint32_t *bs;      // [Z] (gfast only, else nullptr)
   uint8_t *reg;      // [Z]
-  uint64_t *ktab;    // [kKtabSize]
+  KEnt *ktab;        // [max(g_max, kKtabSize)]
+  double *lnv;       // [kLnTab] ln(v)
   unsigned long long *sums;  // [0] S_Z, [1] V_Z, [2] slide block counter,
                              // [3] S partial, [4] V partial
 };
@@ -77,7 +125,7 @@ cudaError_t launch_scan(const Dims &d, const DevState &s, bool gfast,
                         const uint32_t *pairs, uint64_t n, cudaStream_t st);
 cudaError_t launch_slide(const Dims &d, const DevState &s, bool gfast,
                          cudaStream_t st);
-cudaError_t launch_estimate(const Dims &d, const DevState &s,
+cudaError_t launch_estimate(const Dims &d, const DevState &s, const EstConst &c,
                             const uint32_t *aips, uint64_t n, float *out,
                             cudaStream_t st);
 
