@@ -144,6 +144,35 @@ VBDR_API int vbdr_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts,
 VBDR_API int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n_hosts,
                        float *h_out, void *stream);
 
+/* Estimates for n_hosts hosts computed straight from a register array that
+ * the caller already holds in device memory, without allocating anything.
+ * The paper has no counterpart of this call; it serves callers that cannot
+ * call cudaMalloc where they need an estimate -- for instance a process whose
+ * device memory is all reserved at start-up by a framework's own allocator,
+ * or a latency-critical loop that forbids allocation once it runs -- and so
+ * cannot create a handle.
+ * d_reg: num_bdr uint8 registers (one per physical BDR, as written by
+ * vbdr_slide: the largest active LBP1, 0 if none); log2_g: b of every host,
+ * 1..9; seed: the A0 the registers were built with; d_aips / d_out: as in
+ * vbdr_estimate.  The result equals vbdr_estimate on a handle whose registers
+ * are d_reg (same FP64 formula, rounded to FP32).
+ * Working memory: a fixed array of about 12.4 KiB compiled into the library
+ * (seed table for g <= 512, ln table, pool-sum accumulators); every GPU that
+ * loads the library holds it until the process exits.  The first call on
+ * each device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it, so make that first call before any
+ * stream capture.  Each call rebuilds the tables for its seed and clears the
+ * accumulators; all calls share the one array, so calls whose work overlaps
+ * on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.
+ * Errors: VBDR_ERANGE (log2_g > 9), VBDR_EINVAL (NULL or misaligned pointer,
+ * log2_g < 1, num_bdr not in (2^log2_g, 2^32]), VBDR_ECUDA. */
+VBDR_API int vbdr_estimate_registers_noalloc(const uint8_t *d_reg, uint64_t num_bdr,
+                                             uint32_t log2_g, uint64_t seed,
+                                             const uint32_t *d_aips, uint64_t n_hosts,
+                                             float *d_out, void *stream);
+
 /* ---- inspection (tests, debugging); these synchronise the stream ---- */
 
 /* Derived sizes: R (DRs per BDR), w (DR bits), words (32-bit DRV words per

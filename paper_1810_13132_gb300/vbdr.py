@@ -51,6 +51,8 @@ _SIGS = {
     "vbdr_copy_pool_sums": (ctypes.c_int, [_VP, ctypes.POINTER(_U64),
                                            ctypes.POINTER(_U64), _VP]),
     "vbdr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "vbdr_estimate_registers_noalloc": (ctypes.c_int, [_VP, _U64, _U32, _U64, _VP, _U64, _VP,
+                                                       _VP]),
 }
 
 _lib = None
@@ -205,6 +207,17 @@ class Vbdr:
         _check("vbdr_copy_pool_sums", self._L.vbdr_copy_pool_sums(
             self._h, ctypes.byref(S), ctypes.byref(V), _stream_ptr(stream)))
         return S.value, V.value
+
+
+def estimate_registers_noalloc(reg, num_bdr: int, log2_g: int, seed: int, aips, out,
+                               stream=None) -> None:
+    """vbdr_estimate_registers_noalloc on device tensors: estimates straight
+    from a register array, with no device allocation inside the library."""
+    L = load()
+    n = aips.numel()
+    _check("vbdr_estimate_registers_noalloc", L.vbdr_estimate_registers_noalloc(
+        reg.data_ptr(), num_bdr, log2_g, seed, aips.data_ptr() if n else None, n,
+        out.data_ptr() if n else None, _stream_ptr(stream)))
 
 
 def _host_ptr(a, width: int):
