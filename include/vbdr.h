@@ -173,6 +173,36 @@ VBDR_API int vbdr_estimate_registers_noalloc(const uint8_t *d_reg, uint64_t num_
                                              const uint32_t *d_aips, uint64_t n_hosts,
                                              float *d_out, void *stream);
 
+/* Register-level state for workloads too large to scan (batched estimation
+ * over millions of hosts): the register array becomes, for every physical
+ * BDR, the largest value among the virtual registers that Alg. 3 maps onto
+ * it -- host d_aips[h]'s virtual index i goes to BDR getPhyIdx(aip, i) -- and
+ * 0 where none maps; the pool sums are recomputed and the handle becomes
+ * ready for vbdr_estimate.  d_vregs[d_offsets[h] + i], i < g(aip), holds host
+ * h's i-th virtual register (uint8, at most 32 - b).  The DRV is not touched:
+ * the next vbdr_slide recomputes the registers from it.
+ * Errors: VBDR_EINVAL, VBDR_ECUDA. */
+VBDR_API int vbdr_load_virtual_registers(vbdr_t h, const uint32_t *d_aips,
+                                         const uint64_t *d_offsets, uint64_t n_hosts,
+                                         const uint8_t *d_vregs, void *stream);
+
+/* Launch shape of vbdr_estimate: lanes cooperating on one host (8, 16, 32)
+ * and threads per block (32..512, multiple of 32).  The estimate is one
+ * persistent launch (one wave of blocks, grid-stride over batches of 32
+ * hosts) whatever the shape; the shape changes only the speed, never the
+ * result.  Default 32 lanes, 256 threads.  Errors: VBDR_EINVAL. */
+VBDR_API int vbdr_set_estimate_launch(vbdr_t h, uint32_t lanes, uint32_t threads);
+
+/* Autotuner of the estimate launch shape (Sec. 4.2's parallel estimation,
+ * batched over hosts of mixed g): times every candidate shape on these hosts
+ * (one warm-up and two timed launches each, writing d_out), keeps the fastest
+ * for later vbdr_estimate calls and reports it in *lanes / *threads (either
+ * may be NULL).  Synchronises the stream.
+ * Errors: VBDR_EINVAL, VBDR_EORDER, VBDR_ECUDA. */
+VBDR_API int vbdr_autotune_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts,
+                                    float *d_out, uint32_t *lanes, uint32_t *threads,
+                                    void *stream);
+
 /* ---- inspection (tests, debugging); these synchronise the stream ---- */
 
 /* Derived sizes: R (DRs per BDR), w (DR bits), words (32-bit DRV words per

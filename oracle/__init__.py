@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         L.orc_get_state.argtypes = [ctypes.c_void_p, u8p, u32p, u8p, u8p]
         L.orc_set_registers.argtypes = [ctypes.c_void_p, u8p]
         L.orc_pool_sums_get.argtypes = [ctypes.c_void_p, u64p, u64p]
+        L.orc_load_virtual_registers.argtypes = [ctypes.c_void_p, u32p, u64p,
+                                                 ctypes.c_uint64, u8p]
         L.orc_hll_alpha.restype = ctypes.c_double
         L.orc_hll_alpha.argtypes = [ctypes.c_double]
         L.orc_hll.restype = ctypes.c_double
@@ -209,10 +211,24 @@ class Oracle:
                             _ptr(now, ctypes.c_uint8))
         return {"dr": dr, "bs": bs, "reg": reg, "now": now}
 
+    def registers(self) -> np.ndarray:
+        reg = np.empty(self.Z, dtype=np.uint8)
+        lib().orc_get_state(self._h, None, None, _ptr(reg, ctypes.c_uint8), None)
+        return reg
+
     def set_registers(self, reg: np.ndarray) -> None:
         reg = np.ascontiguousarray(reg, dtype=np.uint8)
         assert reg.shape == (self.Z,)
         lib().orc_set_registers(self._h, _ptr(reg, ctypes.c_uint8))
+
+    def load_virtual_registers(self, aips: np.ndarray, offsets: np.ndarray,
+                               vregs: np.ndarray) -> None:
+        aips = np.ascontiguousarray(aips, dtype=np.uint32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        vregs = np.ascontiguousarray(vregs, dtype=np.uint8)
+        lib().orc_load_virtual_registers(self._h, _ptr(aips, ctypes.c_uint32),
+                                         _ptr(offsets, ctypes.c_uint64), aips.size,
+                                         _ptr(vregs, ctypes.c_uint8))
 
     def pool_sums(self) -> tuple[int, int]:
         S, V = ctypes.c_uint64(), ctypes.c_uint64()

@@ -363,6 +363,26 @@ void orc_set_registers(orc_t *o, const uint8_t *reg_in) {
   if (o->slices_closed == 0) o->slices_closed = 1;
 }
 
+/* Register-level synthetic state, for workloads too large to scan: every
+ * physical register becomes the largest of the virtual register values that
+ * Alg. 3 maps onto it (host aips[h]'s virtual index i goes to BDR
+ * getPhyIdx(aips[h], i)); registers no virtual register maps to are 0.
+ * vregs[offsets[h] + i], i < g(aips[h]), is host h's i-th value. */
+void orc_load_virtual_registers(orc_t *o, const uint32_t *aips, const uint64_t *offsets,
+                                uint64_t n, const uint8_t *vregs) {
+  memset(o->reg, 0, (size_t)o->Z);
+  for (uint64_t h = 0; h < n; ++h) {
+    uint32_t g = 1u << orc_host_b(o, aips[h]);
+    for (uint32_t i = 0; i < g; ++i) {
+      uint64_t j = orc_get_phy_idx(o, aips[h], i);
+      uint8_t v = vregs[offsets[h] + i];
+      if (v > o->reg[j]) o->reg[j] = v;
+    }
+  }
+  orc_pool_sums(o);
+  if (o->slices_closed == 0) o->slices_closed = 1;
+}
+
 void orc_pool_sums_get(const orc_t *o, uint64_t *S_Z, uint64_t *V_Z) {
   *S_Z = o->S_Z;
   *V_Z = o->V_Z;

@@ -18,6 +18,7 @@ struct vbdr {
   Dims d;
   DevState s;
   vbk::EstConst est;
+  vbk::EstLaunch est_cfg;  // estimate launch shape (autotuned or set)
   int layout;
   int device;
   int sticky;          // first CUDA error seen (VBDR_ECUDA once set)
@@ -170,7 +171,7 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   e = cudaMalloc(&h->s.drv, (size_t)d.P * d.Zs * sizeof(uint32_t));
   if (e == cudaSuccess && h->layout == VBDR_GFAST)
     e = cudaMalloc(&h->s.bs, (size_t)d.Z * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&h->s.reg, (size_t)d.Z);
+  if (e == cudaSuccess) e = cudaMalloc(&h->s.reg, (size_t)d.Zs);  // whole 32-bit words
   if (e == cudaSuccess) e = cudaMalloc(&h->s.ktab, (size_t)kn * sizeof(vbk::KEnt));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.lnv, vbk::kLnTab * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.sums, 8 * sizeof(unsigned long long));
@@ -181,6 +182,7 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
     e = cudaMemcpy(h->s.lnv, lnv, sizeof(lnv), cudaMemcpyHostToDevice);
   }
   fill_est_const(d, &h->est);
+  h->est_cfg = vbk::kEstCandidates[0];
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_state(h);
@@ -294,7 +296,7 @@ int vbdr_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n, float *d_out,
   if (!d_aips || !d_out || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_out & 3u))
     return VBDR_EINVAL;
   return fail_cuda(h, vbk::launch_estimate(h->d, h->s, h->est, d_aips, n, d_out,
-                                            (cudaStream_t)stream));
+                                            (cudaStream_t)stream, h->est_cfg));
 }
 
 int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n, float *h_out,
@@ -323,9 +325,72 @@ int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n, float *h_ou
     h->est_cap = n;
   }
   e = cudaMemcpyAsync(h->d_aips, h_aips, n * 4, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = vbk::launch_estimate(h->d, h->s, h->est, h->d_aips, n, h->d_out, st);
+  if (e == cudaSuccess) e = vbk::launch_estimate(h->d, h->s, h->est, h->d_aips, n, h->d_out, st, h->est_cfg);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, h->d_out, n * 4, cudaMemcpyDeviceToHost, st);
   return fail_cuda(h, e);
+}
+
+int vbdr_load_virtual_registers(vbdr_t h, const uint32_t *d_aips, const uint64_t *d_offsets,
+                                uint64_t n_hosts, const uint8_t *d_vregs, void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (n_hosts && (!d_aips || !d_offsets || !d_vregs)) return VBDR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = vbk::launch_load_virtual(h->d, h->s, d_aips, d_offsets, n_hosts, d_vregs, st);
+  if (e == cudaSuccess) e = vbk::launch_pool_sums(h->s.reg, h->d.Z, h->s.sums, st);
+  int rc = fail_cuda(h, e);
+  if (rc == VBDR_OK) h->slid = true;
+  return rc;
+}
+
+int vbdr_set_estimate_launch(vbdr_t h, uint32_t lanes, uint32_t threads) {
+  if (!h) return VBDR_EINVAL;
+  if ((lanes != 8 && lanes != 16 && lanes != 32) || threads < 32 || threads > 512 ||
+      threads % 32)
+    return VBDR_EINVAL;
+  h->est_cfg = vbk::EstLaunch{(int)lanes, (int)threads};
+  return VBDR_OK;
+}
+
+int vbdr_autotune_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts, float *d_out,
+                           uint32_t *lanes, uint32_t *threads, void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!h->slid) return VBDR_EORDER;
+  if (n_hosts == 0 || !d_aips || !d_out) return VBDR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail_cuda(h, cudaErrorUnknown);
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail_cuda(h, cudaErrorUnknown);
+  }
+  float best = 1e30f;
+  vbk::EstLaunch best_cfg = vbk::kEstCandidates[0];
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < vbk::kNumEstCandidates && e == cudaSuccess; ++c) {
+    const vbk::EstLaunch cfg = vbk::kEstCandidates[c];
+    // one untimed launch, then the mean of two timed launches
+    e = vbk::launch_estimate(h->d, h->s, h->est, d_aips, n_hosts, d_out, st, cfg);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+      e = vbk::launch_estimate(h->d, h->s, h->est, d_aips, n_hosts, d_out, st, cfg);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && ms < best) {
+      best = ms;
+      best_cfg = cfg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail_cuda(h, e);
+  h->est_cfg = best_cfg;
+  if (lanes) *lanes = (uint32_t)best_cfg.lanes;
+  if (threads) *threads = (uint32_t)best_cfg.threads;
+  return VBDR_OK;
 }
 
 int vbdr_copy_state(vbdr_t h, uint8_t *h_dr, uint32_t *h_bs, uint8_t *h_reg,

@@ -3,13 +3,15 @@
 // Sec. 4.1 cites; Sec. 4.2: registers are read-only here, so any number of
 // hosts are estimated in parallel).
 //
-// Work split: a warp owns a batch of 32 hosts.
-//   gather : for each host of the batch in turn, the 32 lanes visit its g
-//            virtual indices (i = lane + 32u), map each to its physical BDR
-//            pidx = H(aip, Z, s1(i)) and gather the byte register reg[pidx]
-//            (8 gathers in flight per lane); the warp sums
-//            S = sum_i 2^(32 - M_i) exactly in 64-bit integers and counts
-//            V = #{M_i = 0}; lane q keeps host q's (S, V).
+// Work split: one persistent wave of blocks; a warp owns a batch of 32 hosts.
+//   gather : groups of T lanes (T = 8, 16 or 32, chosen per workload by the
+//            autotuner of api.cu) take the batch's hosts in turn; the T lanes
+//            of a group visit the host's g virtual indices (i = sub + T u),
+//            map each to its physical BDR pidx = H(aip, Z, s1(i)) and gather
+//            the byte register reg[pidx] (8 gathers in flight per lane); the
+//            group sums S = sum_i 2^(32 - M_i) exactly in 64-bit integers and
+//            counts V = #{M_i = 0}.  Hosts of mixed g (64..512) share a
+//            launch; small T keeps lanes busy on small g.
 //   finish : every lane evaluates its own host's estimate in FP64, so the
 //            (slow) FP64 pipe runs with all 32 lanes busy:
 //              n_g = HLL(g, S, V), n_Z = HLL(Z, S_Z, V_Z) (once per block),
@@ -26,25 +28,27 @@
 namespace vbk {
 namespace {
 
-constexpr int kEstThreads = 256;
+constexpr int kMaxEstWarps = 16;  // blocks of up to 512 threads
 constexpr int kGatherUnroll = 8;
 
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__global__ void __launch_bounds__(kEstThreads)
+// A warp owns a batch of 32 hosts and splits its lanes into 32/T groups of
+// T lanes; in T steps each group gathers one host of the batch.  The host
+// results land in shared memory so that lane q finishes host q.
+template <bool SMEM_KT, int T>  // seed table staged in shared memory (g_max <= 512)
+__global__ void __launch_bounds__(kMaxEstWarps * 32)
     estimate_kernel(const uint32_t *__restrict__ aips, uint64_t n,
                     float *__restrict__ out, Dims d, DevState s, EstConst c) {
-  __shared__ KEnt kt_s[kKtabSize];
+  static_assert(T == 8 || T == 16 || T == 32, "lanes per host");
+  constexpr uint32_t G = 32 / T;  // hosts gathered at once per warp
+  __shared__ KEnt kt_s[SMEM_KT ? kKtabSize : 1];
   __shared__ double lnv_s[kLnTab];
   __shared__ double nZZ_s;
-  const uint32_t gmax = 1u << (d.group_rule ? d.b_min + 3 : d.b);
-  const bool kt_in_smem = gmax <= (uint32_t)kKtabSize;
-  if (kt_in_smem)
+  __shared__ unsigned long long resS[kMaxEstWarps][32];
+  __shared__ uint32_t resV[kMaxEstWarps][32];
+  if constexpr (SMEM_KT) {
+    const uint32_t gmax = 1u << (d.group_rule ? d.b_min + 3 : d.b);
     for (uint32_t i = threadIdx.x; i < gmax; i += blockDim.x) kt_s[i] = s.ktab[i];
+  }
   for (uint32_t i = threadIdx.x; i < (uint32_t)kLnTab; i += blockDim.x) lnv_s[i] = s.lnv[i];
   if (threadIdx.x == 0) {
     // pool noise term n_Z / Z from the sums of the last slide
@@ -55,28 +59,31 @@ __global__ void __launch_bounds__(kEstThreads)
     nZZ_s = E / Z;
   }
   __syncthreads();
-  const KEnt *kt = kt_in_smem ? kt_s : s.ktab;
+  const KEnt *kt = SMEM_KT ? kt_s : s.ktab;
   const double nZZ = nZZ_s;
   const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t wib = threadIdx.x >> 5;
+  const uint32_t grp = lane / T, sub = lane % T;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
 
   for (uint64_t hb = warp * 32; hb < n; hb += warps * 32) {
     const uint64_t h_l = hb + lane;
     const uint32_t aip_l = h_l < n ? __ldg(aips + h_l) : 0u;
     const uint32_t nb = (n - hb) < 32 ? (uint32_t)(n - hb) : 32u;
-    unsigned long long myS = 0;
-    uint32_t myV = 0;
-    for (uint32_t q = 0; q < nb; ++q) {
-      const uint32_t aip = __shfl_sync(0xffffffffu, aip_l, q);
-      const uint32_t g = 1u << host_b(d, aip);
+#pragma unroll 1
+    for (uint32_t t = 0; t < T; ++t) {
+      const uint32_t j = grp + G * t;  // batch slot this group gathers now
+      const uint32_t aip = __shfl_sync(0xffffffffu, aip_l, j & 31u);
+      const bool valid = j < nb;
+      const uint32_t g = valid ? 1u << host_b(d, aip) : 0u;
       unsigned long long S = 0;
       uint32_t V = 0;
-      for (uint32_t base = 0; base < g; base += 32 * kGatherUnroll) {
+      for (uint32_t base = 0; base < g; base += T * kGatherUnroll) {
         uint32_t M[kGatherUnroll];
 #pragma unroll
         for (int u = 0; u < kGatherUnroll; ++u) {
-          const uint32_t i = base + 32u * u + lane;
+          const uint32_t i = base + T * u + sub;
           M[u] = 0xffu;
           if (i < g) {
             const uint32_t pidx = reduce32(hash32(aip, kt[i]), d.zmul);
@@ -91,14 +98,20 @@ __global__ void __launch_bounds__(kEstThreads)
           }
         }
       }
-      S = warp_sum_u64(S);
-      V = __reduce_add_sync(0xffffffffu, V);
-      if (lane == q) {
-        myS = S;
-        myV = V;
+#pragma unroll
+      for (int o = T / 2; o > 0; o >>= 1) {
+        S += __shfl_xor_sync(0xffffffffu, S, o, T);
+        V += __shfl_xor_sync(0xffffffffu, V, o, T);
+      }
+      if (sub == 0 && valid) {
+        resS[wib][j] = S;
+        resV[wib][j] = V;
       }
     }
+    __syncwarp();
     if (h_l < n) {
+      const unsigned long long myS = resS[wib][lane];
+      const uint32_t myV = resV[wib][lane];
       const uint32_t b = host_b(d, aip_l);
       const double g = (double)(1u << b);
       double n_g = c.amm[b] / ldexp((double)myS, -32);
@@ -108,26 +121,44 @@ __global__ void __launch_bounds__(kEstThreads)
       if (!(est > 0.0)) est = 0.0;
       out[h_l] = (float)est;
     }
+    __syncwarp();
+  }
+}
+
+template <bool SMEM_KT>
+void *estimate_kernel_ptr(int T) {
+  switch (T) {
+    case 8: return (void *)estimate_kernel<SMEM_KT, 8>;
+    case 16: return (void *)estimate_kernel<SMEM_KT, 16>;
+    default: return (void *)estimate_kernel<SMEM_KT, 32>;
   }
 }
 
 }  // namespace
 
+const EstLaunch kEstCandidates[kNumEstCandidates] = {
+    {32, 256}, {16, 256}, {8, 256}, {32, 128}, {16, 128},
+    {8, 128},  {32, 512}, {16, 512}, {8, 512}};
+
 cudaError_t launch_estimate(const Dims &d, const DevState &s, const EstConst &c,
                             const uint32_t *aips, uint64_t n, float *out,
-                            cudaStream_t st) {
+                            cudaStream_t st, EstLaunch cfg) {
   if (n == 0) return cudaSuccess;
+  const int threads = cfg.threads;
+  if (threads < 32 || threads > kMaxEstWarps * 32 || threads % 32) return cudaErrorInvalidValue;
+  const bool smem_kt = (1u << (d.group_rule ? d.b_min + 3 : d.b)) <= (uint32_t)kKtabSize;
+  void *kern = smem_kt ? estimate_kernel_ptr<true>(cfg.lanes) : estimate_kernel_ptr<false>(cfg.lanes);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, estimate_kernel, kEstThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
   if (per_sm < 1) per_sm = 1;
-  const uint64_t hosts_per_block = (kEstThreads / 32) * 32;
+  const uint64_t hosts_per_block = (uint64_t)(threads / 32) * 32;
   const uint64_t want = (n + hosts_per_block - 1) / hosts_per_block;
-  uint64_t grid = (uint64_t)sms * per_sm;
+  uint64_t grid = (uint64_t)sms * per_sm;  // persistent: one wave, grid-stride
   if (want < grid) grid = want;
-  estimate_kernel<<<(unsigned)grid, kEstThreads, 0, st>>>(aips, n, out, d, s, c);
-  return cudaGetLastError();
+  void *args[] = {(void *)&aips, (void *)&n, (void *)&out, (void *)&d, (void *)&s, (void *)&c};
+  return cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(threads), args, 0, st);
 }
 
 }  // namespace vbk

@@ -161,6 +161,6 @@ extern "C" int vbdr_estimate_registers_noalloc(const uint8_t *d_reg, uint64_t nu
   noalloc_pool_sums_kernel<<<(unsigned)grid, 256, 0, st>>>(d_reg, num_bdr, sc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return VBDR_ECUDA;
-  e = launch_estimate(d, s, c, d_aips, n_hosts, d_out, st);
+  e = launch_estimate(d, s, c, d_aips, n_hosts, d_out, st, kEstCandidates[0]);
   return e == cudaSuccess ? VBDR_OK : VBDR_ECUDA;
 }

@@ -77,16 +77,21 @@ __device__ __forceinline__ void pair_update(const Dims &d, const KEnt *kt, uint3
   }
 }
 
-template <int W, bool MIXED>  // W = 0: gfast; W = DR width: gsmall
+// SMEM_KT: the seed table (g_max <= 512 entries) is staged in shared memory
+// and read with shared-memory loads; otherwise it is read from global memory.
+template <int W, bool MIXED, bool SMEM_KT>  // W = 0: gfast; W = DR width: gsmall
 __global__ void __launch_bounds__(kScanThreads)
     scan_kernel(const uint4 *__restrict__ pairs2, uint64_t n_pairs, Dims d, DevState s) {
-  __shared__ KEnt kt_s[kKtabSize];
-  const uint32_t gmax = 1u << (MIXED ? d.b_min + 3 : d.b);
-  const bool kt_in_smem = gmax <= (uint32_t)kKtabSize;
-  if (kt_in_smem)
+  __shared__ KEnt kt_s[SMEM_KT ? kKtabSize : 1];
+  const KEnt *kt;
+  if constexpr (SMEM_KT) {
+    const uint32_t gmax = 1u << (MIXED ? d.b_min + 3 : d.b);
     for (uint32_t i = threadIdx.x; i < gmax; i += blockDim.x) kt_s[i] = s.ktab[i];
-  __syncthreads();
-  const KEnt *kt = kt_in_smem ? kt_s : s.ktab;
+    __syncthreads();
+    kt = kt_s;
+  } else {
+    kt = s.ktab;
+  }
   uint32_t *const state = (W == 0) ? s.bs : s.drv;
 
   const uint64_t units = n_pairs >> 1;  // whole 16-byte loads
@@ -142,17 +147,18 @@ __global__ void __launch_bounds__(kScanThreads)
 template <int W, bool MIXED>
 cudaError_t launch_scan_t(const Dims &d, const DevState &s, const uint32_t *pairs, uint64_t n,
                           cudaStream_t st) {
+  const bool smem_kt = (1u << (MIXED ? d.b_min + 3 : d.b)) <= (uint32_t)kKtabSize;
+  auto kern = smem_kt ? scan_kernel<W, MIXED, true> : scan_kernel<W, MIXED, false>;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel<W, MIXED>, kScanThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScanThreads, 0);
   if (per_sm < 1) per_sm = 1;
   const uint64_t units = n >> 1;
   const uint64_t want = (units + kScanThreads - 1) / kScanThreads;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (want < grid) grid = want ? want : 1;
-  scan_kernel<W, MIXED><<<(unsigned)grid, kScanThreads, 0, st>>>(
-      reinterpret_cast<const uint4 *>(pairs), n, d, s);
+  kern<<<(unsigned)grid, kScanThreads, 0, st>>>(reinterpret_cast<const uint4 *>(pairs), n, d, s);
   return cudaGetLastError();
 }
 

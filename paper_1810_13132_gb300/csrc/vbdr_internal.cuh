@@ -125,8 +125,23 @@ cudaError_t launch_scan(const Dims &d, const DevState &s, bool gfast,
                         const uint32_t *pairs, uint64_t n, cudaStream_t st);
 cudaError_t launch_slide(const Dims &d, const DevState &s, bool gfast,
                          cudaStream_t st);
+// Launch shape of the estimate kernel: lanes cooperating on one host and
+// threads per block.  kEstCandidates is the autotuner's search space; the
+// first entry is the default.
+struct EstLaunch {
+  int lanes;
+  int threads;
+};
+constexpr int kNumEstCandidates = 9;
+extern const EstLaunch kEstCandidates[kNumEstCandidates];
+
 cudaError_t launch_estimate(const Dims &d, const DevState &s, const EstConst &c,
                             const uint32_t *aips, uint64_t n, float *out,
-                            cudaStream_t st);
+                            cudaStream_t st, EstLaunch cfg);
+cudaError_t launch_load_virtual(const Dims &d, const DevState &s, const uint32_t *aips,
+                                const uint64_t *offsets, uint64_t n, const uint8_t *vregs,
+                                cudaStream_t st);
+cudaError_t launch_pool_sums(const uint8_t *reg, uint64_t Z, unsigned long long *sums,
+                             cudaStream_t st);
 
 }  // namespace vbk

@@ -51,6 +51,10 @@ _SIGS = {
     "vbdr_copy_pool_sums": (ctypes.c_int, [_VP, ctypes.POINTER(_U64),
                                            ctypes.POINTER(_U64), _VP]),
     "vbdr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "vbdr_load_virtual_registers": (ctypes.c_int, [_VP, _VP, _VP, _U64, _VP, _VP]),
+    "vbdr_set_estimate_launch": (ctypes.c_int, [_VP, _U32, _U32]),
+    "vbdr_autotune_estimate": (ctypes.c_int, [_VP, _VP, _U64, _VP, ctypes.POINTER(_U32),
+                                              ctypes.POINTER(_U32), _VP]),
     "vbdr_estimate_registers_noalloc": (ctypes.c_int, [_VP, _U64, _U32, _U64, _VP, _U64, _VP,
                                                        _VP]),
 }
@@ -185,6 +189,28 @@ class Vbdr:
         assert n == n2
         _check("vbdr_estimate_host", self._L.vbdr_estimate_host(
             self._h, pa, n, po, _stream_ptr(stream)))
+
+    # -- batched estimation --------------------------------------------------------
+    def load_virtual_registers(self, aips, offsets, vregs, stream=None) -> None:
+        """Register-level state (device tensors: int32 aips, int64 offsets,
+        uint8 virtual registers, host-major)."""
+        _check("vbdr_load_virtual_registers", self._L.vbdr_load_virtual_registers(
+            self._h, aips.data_ptr(), offsets.data_ptr(), aips.numel(), vregs.data_ptr(),
+            _stream_ptr(stream)))
+
+    def set_estimate_launch(self, lanes: int, threads: int) -> None:
+        _check("vbdr_set_estimate_launch", self._L.vbdr_set_estimate_launch(
+            self._h, lanes, threads))
+
+    def autotune_estimate(self, aips, out=None, stream=None) -> tuple[int, int]:
+        import torch
+        if out is None:
+            out = torch.empty(aips.numel(), dtype=torch.float32, device=aips.device)
+        lanes, threads = ctypes.c_uint32(), ctypes.c_uint32()
+        _check("vbdr_autotune_estimate", self._L.vbdr_autotune_estimate(
+            self._h, aips.data_ptr(), aips.numel(), out.data_ptr(), ctypes.byref(lanes),
+            ctypes.byref(threads), _stream_ptr(stream)))
+        return lanes.value, threads.value
 
     # -- inspection --------------------------------------------------------------
     def state(self, stream=None) -> dict:
