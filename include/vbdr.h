@@ -203,6 +203,70 @@ VBDR_API int vbdr_autotune_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n
                                     float *d_out, uint32_t *lanes, uint32_t *threads,
                                     void *stream);
 
+/* ---- learned correction (not in the paper) ----
+ * A 2 x 64 GELU MLP maps a host's feature vector to delta, a correction of
+ * the plain estimate in log space: n = exp(ln(1 + n_plain) + delta) - 1.
+ * Features (80 inputs): x[v] = #{virtual registers of value v} / g for
+ * v = 0..63, x[64] = b/16, x[65] = ln(1 + n_plain)/16, x[66] = ln(1 + n_g)/16
+ * (the host's own HLL estimate), x[67] = ln(1 + n_Z/Z), x[68] = V_Z/Z,
+ * x[69] = V/g, x[70..79] = 0.  Registers never exceed 31, so bins 32..63 are
+ * always 0; device feature matrices carry the 48 live inputs per row as BF16:
+ * x[0..31] then x[64..79].  Weights BF16, accumulation FP32 (tensor cores),
+ * FP32 master parameters trained by AdamW on the GPU.  Parameters travel as
+ * a flat FP32 vector: W1 [64][80] row-major, b1 [64], W2 [64][64], b2 [64],
+ * w3 [64], b3 [1] (vbdr_mlp_num_params() floats).  Hosts whose plain
+ * estimate exceeds nmax keep the plain estimate (the range the network was
+ * trained on). */
+typedef struct vbdr_mlp *vbdr_mlp_t;
+
+VBDR_API int vbdr_mlp_num_params(void);
+
+/* New network on the current device, weights drawn from a seeded uniform
+ * (He) initialisation, biases 0, nmax = +inf.  Errors: VBDR_EINVAL,
+ * VBDR_ENOMEM. */
+VBDR_API int vbdr_mlp_create(uint64_t seed, vbdr_mlp_t *out);
+VBDR_API int vbdr_mlp_destroy(vbdr_mlp_t m);
+
+/* Replace / read the FP32 parameters (host buffers of vbdr_mlp_num_params()
+ * floats) and nmax.  set resets the optimizer state.  Synchronous. */
+VBDR_API int vbdr_mlp_set_params(vbdr_mlp_t m, const float *h_params, float nmax);
+VBDR_API int vbdr_mlp_get_params(vbdr_mlp_t m, float *h_params, float *nmax);
+
+/* Train on n samples: d_X BF16 [n][48] live features (device), d_y FP32 [n]
+ * targets delta* = ln(1 + c) - ln(1 + n_plain) (device); loss = mean squared
+ * error; `epochs` passes of contiguous batches of `batch` samples (shuffle
+ * the set beforehand), AdamW (beta 0.9/0.999, eps 1e-8) with learning rate lr
+ * and decoupled weight decay on the weight matrices.  h_epoch_loss (host,
+ * `epochs` floats, may be NULL) receives each epoch's mean loss.  Synchronises
+ * the stream once per epoch when h_epoch_loss is given.
+ * Errors: VBDR_EINVAL, VBDR_ECUDA. */
+VBDR_API int vbdr_mlp_train(vbdr_mlp_t m, const uint16_t *d_X, const float *d_y, uint64_t n,
+                            uint32_t epochs, uint32_t batch, float lr, float weight_decay,
+                            uint64_t shuffle_seed, float *h_epoch_loss, void *stream);
+
+/* Gradient of the mean squared error over n samples at the current
+ * parameters (h_grad: vbdr_mlp_num_params() floats, host) and the loss.
+ * Synchronous.  For checking the backward kernels. */
+VBDR_API int vbdr_mlp_gradient(vbdr_mlp_t m, const uint16_t *d_X, const float *d_y, uint64_t n,
+                               float *h_grad, float *h_loss, void *stream);
+
+/* delta for n feature rows (d_X BF16 [n][48], d_delta FP32 [n], device). */
+VBDR_API int vbdr_mlp_forward(vbdr_mlp_t m, const uint16_t *d_X, uint64_t n, float *d_delta,
+                              void *stream);
+
+/* Feature rows of n hosts from the handle's registers (d_X BF16 [n][48],
+ * device) and their plain estimates (d_plain FP32 [n], device, may be NULL).
+ * Errors: as vbdr_estimate. */
+VBDR_API int vbdr_features(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts, uint16_t *d_X,
+                           float *d_plain, void *stream);
+
+/* vbdr_estimate with the learned correction fused into the same kernel:
+ * the gather also builds each host's register histogram, the MLP runs on the
+ * tensor cores per batch of 32 hosts, and d_out receives the corrected
+ * estimate (the plain one where n_plain > nmax).  Errors: as vbdr_estimate. */
+VBDR_API int vbdr_estimate_learned(vbdr_t h, vbdr_mlp_t m, const uint32_t *d_aips,
+                                   uint64_t n_hosts, float *d_out, void *stream);
+
 /* ---- inspection (tests, debugging); these synchronise the stream ---- */
 
 /* Derived sizes: R (DRs per BDR), w (DR bits), words (32-bit DRV words per

@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         L.orc_get_state.argtypes = [ctypes.c_void_p, u8p, u32p, u8p, u8p]
         L.orc_set_registers.argtypes = [ctypes.c_void_p, u8p]
         L.orc_pool_sums_get.argtypes = [ctypes.c_void_p, u64p, u64p]
+        L.orc_features.restype = ctypes.c_int
+        L.orc_features.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, f64p, f64p]
         L.orc_load_virtual_registers.argtypes = [ctypes.c_void_p, u32p, u64p,
                                                  ctypes.c_uint64, u8p]
         L.orc_hll_alpha.restype = ctypes.c_double
@@ -191,6 +193,17 @@ class Oracle:
         if rc != 0:
             raise RuntimeError("estimate before the first slide")
         return out
+
+    def features(self, aips: np.ndarray):
+        """(X [n, 80] float64, n_plain [n]) of the learned correction."""
+        aips = np.ascontiguousarray(aips, dtype=np.uint32)
+        X = np.empty((aips.size, 80), dtype=np.float64)
+        est = np.empty(aips.size, dtype=np.float64)
+        rc = lib().orc_features(self._h, _ptr(aips, ctypes.c_uint32), aips.size,
+                                _ptr(X, ctypes.c_double), _ptr(est, ctypes.c_double))
+        if rc != 0:
+            raise RuntimeError("features before the first slide")
+        return X, est
 
     def host_registers(self, aip: int):
         """(S, V, sum_lbp1, hist64) of one host's virtual registers."""

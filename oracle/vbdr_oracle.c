@@ -326,6 +326,44 @@ void orc_host_registers(const orc_t *o, uint32_t aip, uint64_t *S,
   if (sum_lbp1) *sum_lbp1 = l;
 }
 
+/* Per-host feature vector of the learned correction (not part of the
+ * paper; its definition is shared by specification with the library):
+ *   x[v]  = #{virtual registers with value v} / g,   v = 0..63
+ *   x[64] = b / 16
+ *   x[65] = ln(1 + n_plain) / 16      (the vHLL estimate)
+ *   x[66] = ln(1 + n_g) / 16          (the host's HLL estimate, noise kept)
+ *   x[67] = ln(1 + n_Z / Z)           (pool load per register)
+ *   x[68] = V_Z / Z                   (pool empty fraction)
+ *   x[69] = V / g                     (host empty fraction)
+ *   x[70..79] = 0
+ * X is [n][80]; n_plain[h] receives the vHLL estimate. */
+int orc_features(const orc_t *o, const uint32_t *aips, uint64_t n, double *X,
+                 double *n_plain) {
+  if (o->slices_closed == 0) return -1;
+  const double Z = (double)o->Z;
+  const double n_Z = orc_hll(Z, o->S_Z, o->V_Z);
+  for (uint64_t h = 0; h < n; ++h) {
+    uint64_t S, V;
+    uint32_t hist[64];
+    orc_host_registers(o, aips[h], &S, &V, NULL, hist);
+    uint32_t b = orc_host_b(o, aips[h]);
+    double g = (double)(1u << b);
+    double n_g = orc_hll(g, S, V);
+    double est = orc_vhll(Z, g, S, V, o->S_Z, o->V_Z);
+    double *x = X + h * 80;
+    for (int v = 0; v < 64; ++v) x[v] = hist[v] / g;
+    x[64] = b / 16.0;
+    x[65] = log1p(est) / 16.0;
+    x[66] = log1p(n_g) / 16.0;
+    x[67] = log1p(n_Z / Z);
+    x[68] = (double)o->V_Z / Z;
+    x[69] = (double)V / g;
+    for (int v = 70; v < 80; ++v) x[v] = 0.0;
+    n_plain[h] = est;
+  }
+  return 0;
+}
+
 /* Estimates of n hosts, FP64.  Returns -1 before the first slide. */
 int orc_estimate(const orc_t *o, const uint32_t *aips, uint64_t n,
                  double *out) {

@@ -330,6 +330,37 @@ int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n, float *h_ou
   return fail_cuda(h, e);
 }
 
+int vbdr_features(vbdr_t h, const uint32_t *d_aips, uint64_t n, uint16_t *d_X, float *d_plain,
+                  void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!h->slid) return VBDR_EORDER;
+  if (n == 0) return VBDR_OK;
+  if (!d_aips || !d_X || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_X & 3u)) return VBDR_EINVAL;
+  float *plain = d_plain;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!plain) {  // the kernel always writes the plain estimates: use the staging buffer
+    if (n > h->est_cap) return VBDR_ERANGE;
+    plain = h->d_out;
+  }
+  return fail_cuda(h, vbk::launch_features(h->d, h->s, h->est, d_aips, n,
+                                           reinterpret_cast<__nv_bfloat16 *>(d_X), plain, st,
+                                           h->est_cfg));
+}
+
+int vbdr_estimate_learned(vbdr_t h, vbdr_mlp_t m, const uint32_t *d_aips, uint64_t n,
+                          float *d_out, void *stream) {
+  if (!h || !m) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!h->slid) return VBDR_EORDER;
+  if (n == 0) return VBDR_OK;
+  if (!d_aips || !d_out || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_out & 3u))
+    return VBDR_EINVAL;
+  return fail_cuda(h, vbk::launch_estimate_learned(h->d, h->s, h->est, d_aips, n, d_out,
+                                                   (cudaStream_t)stream, h->est_cfg,
+                                                   vbk::mlp_weights(m), vbk::mlp_nmax(m)));
+}
+
 int vbdr_load_virtual_registers(vbdr_t h, const uint32_t *d_aips, const uint64_t *d_offsets,
                                 uint64_t n_hosts, const uint8_t *d_vregs, void *stream) {
   if (!h) return VBDR_EINVAL;

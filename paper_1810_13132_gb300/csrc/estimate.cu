@@ -23,6 +23,7 @@
 //            linear-counting decision are computed with the same IEEE
 //            operations as the plain formula, so the decision is exact.
 //            The result is rounded to FP32.
+#include "mlp_device.cuh"
 #include "vbdr_internal.cuh"
 
 namespace vbk {
@@ -30,21 +31,37 @@ namespace {
 
 constexpr int kMaxEstWarps = 16;  // blocks of up to 512 threads
 constexpr int kGatherUnroll = 8;
+constexpr int kLearnedWarps = 4;  // block shape of the feature / learned modes
+
+// What the kernel produces per host.
+enum EstMode { kPlain = 0, kFeatures = 1, kLearned = 2 };
 
 // A warp owns a batch of 32 hosts and splits its lanes into 32/T groups of
 // T lanes; in T steps each group gathers one host of the batch.  The host
 // results land in shared memory so that lane q finishes host q.
-template <bool SMEM_KT, int T>  // seed table staged in shared memory (g_max <= 512)
-__global__ void __launch_bounds__(kMaxEstWarps * 32)
+// kFeatures / kLearned also count each host's register values: every lane
+// keeps a private 32-bin byte histogram (a shared-memory row of 36 bytes, so
+// the 32 lanes' rows fall in distinct banks), the group adds its rows per bin
+// and writes bin / g into the batch's BF16 feature tile; the finishing lane
+// adds the noise statistics.  kLearned then runs the MLP on the tile
+// (mma.sync, 32 hosts per warp) and corrects the estimate.
+template <bool SMEM_KT, int T, int MODE>  // seed table in shared memory (g_max <= 512)
+__global__ void __launch_bounds__(MODE == kPlain ? kMaxEstWarps * 32 : kLearnedWarps * 32)
     estimate_kernel(const uint32_t *__restrict__ aips, uint64_t n,
-                    float *__restrict__ out, Dims d, DevState s, EstConst c) {
+                    float *__restrict__ out, Dims d, DevState s, EstConst c,
+                    MlpDevWeights mw, float nmax, __nv_bfloat16 *__restrict__ feat_out) {
   static_assert(T == 8 || T == 16 || T == 32, "lanes per host");
   constexpr uint32_t G = 32 / T;  // hosts gathered at once per warp
+  constexpr int WARPS = MODE == kPlain ? kMaxEstWarps : kLearnedWarps;
+  constexpr bool HIST = MODE != kPlain;
   __shared__ KEnt kt_s[SMEM_KT ? kKtabSize : 1];
   __shared__ double lnv_s[kLnTab];
   __shared__ double nZZ_s;
-  __shared__ unsigned long long resS[kMaxEstWarps][32];
-  __shared__ uint32_t resV[kMaxEstWarps][32];
+  __shared__ unsigned long long resS[WARPS][32];
+  __shared__ uint32_t resV[WARPS][32];
+  __shared__ uint32_t hrow[HIST ? WARPS : 1][32][9];                    // private histograms
+  __shared__ __align__(16) __nv_bfloat16 ftile[HIST ? WARPS : 1][32][kMlpLive];
+  __shared__ __align__(16) __nv_bfloat16 h1tile[MODE == kLearned ? WARPS : 1][32][kMlpHid];
   if constexpr (SMEM_KT) {
     const uint32_t gmax = 1u << (d.group_rule ? d.b_min + 3 : d.b);
     for (uint32_t i = threadIdx.x; i < gmax; i += blockDim.x) kt_s[i] = s.ktab[i];
@@ -79,6 +96,10 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
       const uint32_t g = valid ? 1u << host_b(d, aip) : 0u;
       unsigned long long S = 0;
       uint32_t V = 0;
+      if constexpr (HIST) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) hrow[wib][lane][q] = 0u;
+      }
       for (uint32_t base = 0; base < g; base += T * kGatherUnroll) {
         uint32_t M[kGatherUnroll];
 #pragma unroll
@@ -95,8 +116,24 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
           if (M[u] != 0xffu) {
             S += 1ull << (32u - M[u]);
             V += (M[u] == 0u);
+            if constexpr (HIST) atomicAdd(&hrow[wib][lane][M[u] >> 2], 1u << (8u * (M[u] & 3u)));
           }
         }
+      }
+      if constexpr (HIST) {
+        __syncwarp();
+        if (valid) {
+          const float inv_g = 1.0f / (float)g;
+#pragma unroll
+          for (uint32_t bb = 0; bb < 32 / T; ++bb) {
+            const uint32_t bin = sub + T * bb;
+            uint32_t cnt = 0;
+            for (uint32_t r = 0; r < T; ++r)
+              cnt += (hrow[wib][grp * T + r][bin >> 2] >> (8u * (bin & 3u))) & 0xffu;
+            ftile[wib][j][bin] = __float2bfloat16((float)cnt * inv_g);
+          }
+        }
+        __syncwarp();
       }
 #pragma unroll
       for (int o = T / 2; o > 0; o >>= 1) {
@@ -119,19 +156,77 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
         n_g = g * (myV < (uint32_t)kLnTab ? c.lng[b] - lnv_s[myV] : log(g / (double)myV));
       double est = c.kz[b] * (ldexp(n_g, -(int)b) - nZZ);
       if (!(est > 0.0)) est = 0.0;
-      out[h_l] = (float)est;
+      if constexpr (MODE == kPlain) {
+        out[h_l] = (float)est;
+      } else {
+        __nv_bfloat16 *x = &ftile[wib][lane][32];
+        x[0] = __float2bfloat16((float)b * 0.0625f);
+        x[1] = __float2bfloat16(log1pf((float)est) * 0.0625f);
+        x[2] = __float2bfloat16(log1pf((float)n_g) * 0.0625f);
+        x[3] = __float2bfloat16(log1pf((float)nZZ));
+        x[4] = __float2bfloat16((float)((double)s.sums[1] / (double)d.Z));
+        x[5] = __float2bfloat16((float)myV / (float)(1u << b));
+#pragma unroll
+        for (int q = 6; q < 16; ++q) x[q] = __float2bfloat16(0.f);
+        resS[wib][lane] = __double_as_longlong(est);
+      }
+    }
+    if constexpr (MODE == kFeatures) {
+      __syncwarp();
+      for (uint32_t i = lane; i < 32 * kMlpLive; i += 32) {
+        const uint64_t r = hb + i / kMlpLive;
+        if (r < n) feat_out[r * kMlpLive + i % kMlpLive] = ftile[wib][i / kMlpLive][i % kMlpLive];
+      }
+      if (h_l < n) out[h_l] = (float)__longlong_as_double(resS[wib][lane]);
+    } else if constexpr (MODE == kLearned) {
+      __syncwarp();
+      if (h_l >= n) {  // rows past the end: defined inputs for the tensor cores
+        for (int q = 0; q < kMlpLive; ++q) ftile[wib][lane][q] = __float2bfloat16(0.f);
+      }
+      __syncwarp();
+      const float delta = mlp_forward_warp(&ftile[wib][0][0], &h1tile[wib][0][0], mw);
+      if (h_l < n) {
+        const float plain = (float)__longlong_as_double(resS[wib][lane]);
+        float corr = expm1f(log1pf(plain) + delta);
+        if (!(corr > 0.f)) corr = 0.f;
+        out[h_l] = plain > nmax ? plain : corr;
+      }
     }
     __syncwarp();
   }
 }
 
-template <bool SMEM_KT>
+template <bool SMEM_KT, int MODE>
 void *estimate_kernel_ptr(int T) {
   switch (T) {
-    case 8: return (void *)estimate_kernel<SMEM_KT, 8>;
-    case 16: return (void *)estimate_kernel<SMEM_KT, 16>;
-    default: return (void *)estimate_kernel<SMEM_KT, 32>;
+    case 8: return (void *)estimate_kernel<SMEM_KT, 8, MODE>;
+    case 16: return (void *)estimate_kernel<SMEM_KT, 16, MODE>;
+    default: return (void *)estimate_kernel<SMEM_KT, 32, MODE>;
   }
+}
+
+template <int MODE>
+cudaError_t launch_mode(const Dims &d, const DevState &s, const EstConst &c, const uint32_t *aips,
+                        uint64_t n, float *out, cudaStream_t st, EstLaunch cfg, MlpDevWeights mw,
+                        float nmax, __nv_bfloat16 *feat) {
+  if (n == 0) return cudaSuccess;
+  const int threads = MODE == kPlain ? cfg.threads : kLearnedWarps * 32;
+  if (threads < 32 || threads > kMaxEstWarps * 32 || threads % 32) return cudaErrorInvalidValue;
+  const bool smem_kt = (1u << (d.group_rule ? d.b_min + 3 : d.b)) <= (uint32_t)kKtabSize;
+  void *kern = smem_kt ? estimate_kernel_ptr<true, MODE>(cfg.lanes)
+                       : estimate_kernel_ptr<false, MODE>(cfg.lanes);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t hosts_per_block = (uint64_t)(threads / 32) * 32;
+  const uint64_t want = (n + hosts_per_block - 1) / hosts_per_block;
+  uint64_t grid = (uint64_t)sms * per_sm;  // persistent: one wave, grid-stride
+  if (want < grid) grid = want;
+  void *args[] = {(void *)&aips, (void *)&n, (void *)&out, (void *)&d, (void *)&s,
+                  (void *)&c,    (void *)&mw, (void *)&nmax, (void *)&feat};
+  return cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(threads), args, 0, st);
 }
 
 }  // namespace
@@ -143,22 +238,19 @@ const EstLaunch kEstCandidates[kNumEstCandidates] = {
 cudaError_t launch_estimate(const Dims &d, const DevState &s, const EstConst &c,
                             const uint32_t *aips, uint64_t n, float *out,
                             cudaStream_t st, EstLaunch cfg) {
-  if (n == 0) return cudaSuccess;
-  const int threads = cfg.threads;
-  if (threads < 32 || threads > kMaxEstWarps * 32 || threads % 32) return cudaErrorInvalidValue;
-  const bool smem_kt = (1u << (d.group_rule ? d.b_min + 3 : d.b)) <= (uint32_t)kKtabSize;
-  void *kern = smem_kt ? estimate_kernel_ptr<true>(cfg.lanes) : estimate_kernel_ptr<false>(cfg.lanes);
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
-  if (per_sm < 1) per_sm = 1;
-  const uint64_t hosts_per_block = (uint64_t)(threads / 32) * 32;
-  const uint64_t want = (n + hosts_per_block - 1) / hosts_per_block;
-  uint64_t grid = (uint64_t)sms * per_sm;  // persistent: one wave, grid-stride
-  if (want < grid) grid = want;
-  void *args[] = {(void *)&aips, (void *)&n, (void *)&out, (void *)&d, (void *)&s, (void *)&c};
-  return cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(threads), args, 0, st);
+  return launch_mode<kPlain>(d, s, c, aips, n, out, st, cfg, MlpDevWeights{}, 0.f, nullptr);
+}
+
+cudaError_t launch_features(const Dims &d, const DevState &s, const EstConst &c,
+                            const uint32_t *aips, uint64_t n, __nv_bfloat16 *feat, float *plain,
+                            cudaStream_t st, EstLaunch cfg) {
+  return launch_mode<kFeatures>(d, s, c, aips, n, plain, st, cfg, MlpDevWeights{}, 0.f, feat);
+}
+
+cudaError_t launch_estimate_learned(const Dims &d, const DevState &s, const EstConst &c,
+                                    const uint32_t *aips, uint64_t n, float *out, cudaStream_t st,
+                                    EstLaunch cfg, MlpDevWeights mw, float nmax) {
+  return launch_mode<kLearned>(d, s, c, aips, n, out, st, cfg, mw, nmax, nullptr);
 }
 
 }  // namespace vbk

@@ -21,6 +21,10 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mlp_device.cuh"
+
+struct vbdr_mlp;
+
 namespace vbk {
 
 constexpr int kMaxLog2G = 16;
@@ -138,6 +142,14 @@ extern const EstLaunch kEstCandidates[kNumEstCandidates];
 cudaError_t launch_estimate(const Dims &d, const DevState &s, const EstConst &c,
                             const uint32_t *aips, uint64_t n, float *out,
                             cudaStream_t st, EstLaunch cfg);
+cudaError_t launch_features(const Dims &d, const DevState &s, const EstConst &c,
+                            const uint32_t *aips, uint64_t n, __nv_bfloat16 *feat, float *plain,
+                            cudaStream_t st, EstLaunch cfg);
+cudaError_t launch_estimate_learned(const Dims &d, const DevState &s, const EstConst &c,
+                                    const uint32_t *aips, uint64_t n, float *out, cudaStream_t st,
+                                    EstLaunch cfg, MlpDevWeights mw, float nmax);
+MlpDevWeights mlp_weights(const vbdr_mlp *m);
+float mlp_nmax(const vbdr_mlp *m);
 cudaError_t launch_load_virtual(const Dims &d, const DevState &s, const uint32_t *aips,
                                 const uint64_t *offsets, uint64_t n, const uint8_t *vregs,
                                 cudaStream_t st);

@@ -55,6 +55,18 @@ _SIGS = {
     "vbdr_set_estimate_launch": (ctypes.c_int, [_VP, _U32, _U32]),
     "vbdr_autotune_estimate": (ctypes.c_int, [_VP, _VP, _U64, _VP, ctypes.POINTER(_U32),
                                               ctypes.POINTER(_U32), _VP]),
+    "vbdr_mlp_num_params": (ctypes.c_int, []),
+    "vbdr_mlp_create": (ctypes.c_int, [_U64, ctypes.POINTER(_VP)]),
+    "vbdr_mlp_destroy": (ctypes.c_int, [_VP]),
+    "vbdr_mlp_set_params": (ctypes.c_int, [_VP, _VP, ctypes.c_float]),
+    "vbdr_mlp_get_params": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_float)]),
+    "vbdr_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, _U64, _U32, _U32, ctypes.c_float,
+                                      ctypes.c_float, _U64, _VP, _VP]),
+    "vbdr_mlp_gradient": (ctypes.c_int, [_VP, _VP, _VP, _U64, _VP,
+                                         ctypes.POINTER(ctypes.c_float), _VP]),
+    "vbdr_mlp_forward": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
+    "vbdr_features": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP, _VP]),
+    "vbdr_estimate_learned": (ctypes.c_int, [_VP, _VP, _VP, _U64, _VP, _VP]),
     "vbdr_estimate_registers_noalloc": (ctypes.c_int, [_VP, _U64, _U32, _U64, _VP, _U64, _VP,
                                                        _VP]),
 }
@@ -212,6 +224,26 @@ class Vbdr:
             ctypes.byref(threads), _stream_ptr(stream)))
         return lanes.value, threads.value
 
+    # -- learned correction ------------------------------------------------------
+    def features(self, aips, stream=None):
+        """(X bf16 [n, 48] live features, plain estimates f32 [n]) on the device."""
+        import torch
+        n = aips.numel()
+        X = torch.empty((n, 48), dtype=torch.bfloat16, device=aips.device)
+        plain = torch.empty(n, dtype=torch.float32, device=aips.device)
+        _check("vbdr_features", self._L.vbdr_features(
+            self._h, aips.data_ptr(), n, X.data_ptr(), plain.data_ptr(), _stream_ptr(stream)))
+        return X, plain
+
+    def estimate_learned(self, mlp: "Mlp", aips, out=None, stream=None):
+        import torch
+        n = aips.numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=aips.device)
+        _check("vbdr_estimate_learned", self._L.vbdr_estimate_learned(
+            self._h, mlp._h, aips.data_ptr(), n, out.data_ptr(), _stream_ptr(stream)))
+        return out
+
     # -- inspection --------------------------------------------------------------
     def state(self, stream=None) -> dict:
         Z = self.cfg.num_bdr
@@ -233,6 +265,75 @@ class Vbdr:
         _check("vbdr_copy_pool_sums", self._L.vbdr_copy_pool_sums(
             self._h, ctypes.byref(S), ctypes.byref(V), _stream_ptr(stream)))
         return S.value, V.value
+
+
+class Mlp:
+    """The learned correction's network (see include/vbdr.h): BF16/FP32
+    tensor-core kernels for training and inference live in the library."""
+
+    def __init__(self, seed: int = 1):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the MLP kernels need a CUDA GPU")
+        self._L = load()
+        h = ctypes.c_void_p()
+        _check("vbdr_mlp_create", self._L.vbdr_mlp_create(seed, ctypes.byref(h)))
+        self._h = h
+        self.n_params = self._L.vbdr_mlp_num_params()
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._L.vbdr_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> tuple[np.ndarray, float]:
+        p = np.empty(self.n_params, dtype=np.float32)
+        nmax = ctypes.c_float()
+        _check("vbdr_mlp_get_params", self._L.vbdr_mlp_get_params(self._h, p.ctypes.data,
+                                                                  ctypes.byref(nmax)))
+        return p, nmax.value
+
+    def set_params(self, params: np.ndarray, nmax: float = 3.0e38) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.n_params
+        _check("vbdr_mlp_set_params", self._L.vbdr_mlp_set_params(self._h, p.ctypes.data, nmax))
+
+    def train(self, X, y, epochs: int, batch: int, lr: float, weight_decay: float = 0.0,
+              stream=None) -> np.ndarray:
+        """X: bf16 [n, 48] CUDA tensor, y: f32 [n] CUDA tensor."""
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check("vbdr_mlp_train", self._L.vbdr_mlp_train(
+            self._h, X.data_ptr(), y.data_ptr(), y.numel(), epochs, batch, lr, weight_decay, 0,
+            losses.ctypes.data, _stream_ptr(stream)))
+        return losses
+
+    def gradient(self, X, y, stream=None) -> tuple[np.ndarray, float]:
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check("vbdr_mlp_gradient", self._L.vbdr_mlp_gradient(
+            self._h, X.data_ptr(), y.data_ptr(), y.numel(), g.ctypes.data, ctypes.byref(loss),
+            _stream_ptr(stream)))
+        return g, loss.value
+
+    def forward(self, X, stream=None):
+        import torch
+        n = X.shape[0]
+        d = torch.empty(n, dtype=torch.float32, device=X.device)
+        _check("vbdr_mlp_forward", self._L.vbdr_mlp_forward(self._h, X.data_ptr(), n,
+                                                            d.data_ptr(), _stream_ptr(stream)))
+        return d
+
+
+def live_features(X80: np.ndarray) -> np.ndarray:
+    """The 48 live columns (bins 0..31, then inputs 64..79) of 80-input rows."""
+    X80 = np.asarray(X80)
+    return np.ascontiguousarray(np.concatenate([X80[:, :32], X80[:, 64:80]], axis=1))
 
 
 def estimate_registers_noalloc(reg, num_bdr: int, log2_g: int, seed: int, aips, out,
