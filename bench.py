@@ -39,7 +39,9 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--layout", default="gfast", choices=["gfast", "gsmall"])
-    p.add_argument("--workload", default="trace", choices=["trace", "small", "batched"])
+    p.add_argument("--workload", default="trace", choices=["trace", "small", "batched", "serve"])
+    p.add_argument("--tenants", type=int, default=2, help="serve: concurrent tenants")
+    p.add_argument("--slices-per-tenant", type=int, default=40, help="serve: timed slices")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mre", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -238,13 +240,44 @@ def run_ours(a):
     ms_step = total_ms / a.steps
     value = (N * ws * a.steps) / (total_ms * 1e-3) / 1e9
 
+    # learned correction (weights trained by tests/train_correction.py): the
+    # fused estimate + MLP kernel timed on the same state as the plain one
+    learned = None
+    wpath = os.path.join(ROOT, "paper_1810_13132_gb300", "weights", "correction_trace.npz")
+    mlp = None
+    if os.path.exists(wpath) and a.workload == "trace":
+        from paper_1810_13132_gb300 import Mlp
+        wz = np.load(wpath)
+        mlp = Mlp(seed=1)
+        mlp.set_params(wz["params"], float(wz["nmax"]))
+        d_out2 = torch.empty(H, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            v.estimate_learned(mlp, d_aips, out=d_out2)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        for _ in range(a.steps):
+            v.estimate(d_aips, out=d_out)
+        ev[1].record(stream)
+        ev[2].record(stream)
+        for _ in range(a.steps):
+            v.estimate_learned(mlp, d_aips, out=d_out2)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        learned = {"estimate_ms_plain": round(ev[0].elapsed_time(ev[1]) / a.steps, 4),
+                   "estimate_ms_learned": round(ev[2].elapsed_time(ev[3]) / a.steps, 4),
+                   "weights": os.path.relpath(wpath, ROOT)}
+
     # accuracy on the state the timed steps left (window = union of the
     # distinct slices once k >= N_DISTINCT_SLICES slices have been scanned)
     mre = None
     if not a.no_mre and rank == 0 and a.warmup + a.steps >= nsl and nsl <= wl["k"]:
         def est_fn(sample):
             return v.estimate(torch.from_numpy(sample.view(np.int32)).cuda()).cpu().numpy()
-        mre = _exact_mre(gen, slices, est_fn)
+        mre = {"plain": _exact_mre(gen, slices, est_fn)}
+        if mlp is not None:
+            def est_fn_l(sample):
+                return v.estimate_learned(mlp, torch.from_numpy(sample.view(np.int32)).cuda()).cpu().numpy()
+            mre["learned"] = _exact_mre(gen, slices, est_fn_l)
 
     # end to end through the host-buffer entry points
     e2e = None
@@ -316,6 +349,7 @@ def run_ours(a):
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic_bytes, "peak_kind": peak_kind},
         "accuracy": mre,
+        "learned_correction": learned,
         "e2e": e2e,
         "gpu_launches": 3 * a.steps,
         "clocks": clocks,
@@ -407,6 +441,104 @@ def run_batched(a):
     v.close()
 
 
+# ------------------------------------------------------ streaming service arm
+
+def run_serve(a):
+    """Streaming service: slices of log-uniform size in [1M, 128M] pairs
+    (8M active hosts, Zipf 1.1 host weights, bursty superspreaders at 0.01%),
+    k = 30, Z = 2^26, g = 256; every slice is one CUDA graph replay of scan +
+    slide + estimate of all 8M hosts + learned correction + copy-back, with
+    several tenants served at once."""
+    import threading
+    import torch
+    from paper_1810_13132_gb300 import Config, Mlp, Server
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    wl = traffic.STREAM
+    rng = np.random.default_rng(7)
+    tenants = []
+    for t in range(a.tenants):
+        st = traffic.StreamingTraffic(wl["n_hosts"], wl["zipf_s"], seed=500 + t)
+        pool = torch.from_numpy(st.make_pool(wl["n_hi"]).view(np.int32)).pin_memory()
+        n_all = a.warmup + a.slices_per_tenant
+        sizes = traffic.log_uniform_sizes(rng, n_all, wl["n_lo"], wl["n_hi"])
+        offs = [int(rng.integers(0, wl["n_hi"] - n + 1)) for n in sizes]
+        tenants.append((st.aips, pool, sizes, offs))
+    mlp = None
+    wpath = os.path.join(ROOT, "paper_1810_13132_gb300", "weights", "correction_trace.npz")
+    if os.path.exists(wpath):
+        wz = np.load(wpath)
+        mlp = Mlp(seed=1)
+        mlp.set_params(wz["params"], float(wz["nmax"]))
+    cfg = Config(k=wl["k"], num_bdr=wl["Z"], log2_g=wl["log2_g"], seed=SEED)
+    srv = Server(budget_bytes=240 << 30, max_tenants=max(4, a.tenants))
+    lat = {"device": [], "e2e": []}
+    pairs_done = [0]
+    lock = threading.Lock()
+    start_evt = threading.Barrier(a.tenants + 1)
+
+    def worker(i):
+        aips, pool, sizes, offs = tenants[i]
+        t = srv.open(cfg, wl["n_hi"], aips, mlp=mlp)
+        out = np.empty(aips.size, dtype=np.float32)
+        pending = []
+
+        def run(j, timed):
+            pending.append((srv.submit(t, pool[offs[j]:offs[j] + int(sizes[j])]), j, timed))
+            if len(pending) == 2:
+                tk, jj, tt = pending.pop(0)
+                dms, ems = srv.wait(t, tk, out)
+                if tt:
+                    with lock:
+                        lat["device"].append(dms)
+                        lat["e2e"].append(ems)
+                        pairs_done[0] += int(sizes[jj])
+
+        for j in range(a.warmup):
+            run(j, False)
+        while pending:
+            srv.wait(t, pending.pop(0)[0], out)
+        start_evt.wait()
+        for j in range(a.warmup, a.warmup + a.slices_per_tenant):
+            run(j, True)
+        while pending:
+            tk, jj, tt = pending.pop(0)
+            dms, ems = srv.wait(t, tk, out)
+            with lock:
+                lat["device"].append(dms)
+                lat["e2e"].append(ems)
+                pairs_done[0] += int(sizes[jj])
+        srv.close_tenant(t)
+
+    th = [threading.Thread(target=worker, args=(i,)) for i in range(a.tenants)]
+    for x in th:
+        x.start()
+    start_evt.wait()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t0 = time.perf_counter()
+        for x in th:
+            x.join()
+        wall = time.perf_counter() - t0
+    dev = np.array(lat["device"])
+    e2e = np.array(lat["e2e"])
+    line = {
+        "metric": "streaming service: sustained G pairs/s; p50/p99 slice latency",
+        "value": round(pairs_done[0] / wall / 1e9, 3), "unit": "G pairs/s",
+        "n_gpus": 1, "steps": len(dev), "warmup": a.warmup * a.tenants,
+        "ms_per_step": round(float(np.mean(e2e)), 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl["name"], "tenants": a.tenants, "hosts_per_tenant": wl["n_hosts"],
+                   "learned_correction": mlp is not None},
+        "latency_ms": {"device_p50": float(np.percentile(dev, 50)), "device_p99": float(np.percentile(dev, 99)),
+                       "e2e_p50": float(np.percentile(e2e, 50)), "e2e_p99": float(np.percentile(e2e, 99))},
+        "pairs": pairs_done[0], "wall_s": round(wall, 3),
+        "gpu_launches": int(len(dev) * 4),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    srv.close()
+
+
 # ------------------------------------------------- oracle (CPU) timings
 
 def _oracle_step_times(wl, gen, slices, n_pairs_sample, n_hosts_sample):
@@ -478,5 +610,7 @@ if __name__ == "__main__":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)

@@ -115,6 +115,13 @@ VBDR_API int vbdr_scan_slice(vbdr_t h, const uint32_t *d_pairs, uint64_t n,
 VBDR_API int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n,
                          void *stream);
 
+/* vbdr_scan_slice with the pair count read from device memory when the
+ * kernel runs: min(*d_n, max_n) pairs of d_pairs are scanned (d_n: one
+ * uint64 on the device, 8-byte aligned).  A CUDA graph captured around this
+ * call serves slices of any size up to max_n.  Errors: as vbdr_scan_slice. */
+VBDR_API int vbdr_scan_slice_devn(vbdr_t h, const uint32_t *d_pairs, const uint64_t *d_n,
+                                  uint64_t max_n, void *stream);
+
 /* Close the current slice (Sec. 3 and 4.2).
  *   gfast : every BDR slides all DRs, sets the DR of the highest set bit of
  *           bsLBP1 (Alg. 6) and clears bsLBP1; then its register is read
@@ -266,6 +273,63 @@ VBDR_API int vbdr_features(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts, u
  * estimate (the plain one where n_plain > nmax).  Errors: as vbdr_estimate. */
 VBDR_API int vbdr_estimate_learned(vbdr_t h, vbdr_mlp_t m, const uint32_t *d_aips,
                                    uint64_t n_hosts, float *d_out, void *stream);
+
+/* ---- streaming service ----
+ * A server runs many VBDR instances ("tenants", e.g. one per monitored
+ * link) on one GPU.  Each tenant keeps its BDR pool on the device for its
+ * whole life and owns a copy stream, a compute stream and two captured CUDA
+ * graphs (one per staging buffer), each holding the full per-slice path:
+ * scan (slice size read from device memory) -> slide -> estimate of the
+ * tenant's hosts (plain, or with the learned correction) -> copy of the
+ * estimates to pinned host memory.  A tenant's slices run in order, two at
+ * most in flight; tenants run concurrently and overlap on the device.
+ * Admission: a tenant's device footprint (vbdr_server_tenant_bytes) must fit
+ * in the server's budget next to the admitted ones; otherwise vbdr_server_open
+ * waits, bounded by its timeout, until tenants close and free memory. */
+typedef struct vbdr_server *vbdr_server_t;
+typedef struct {
+  uint64_t device_budget_bytes; /* device memory all tenants may hold together */
+  uint32_t max_tenants;         /* 1..1024 */
+  uint32_t reserved;            /* must be 0 */
+} vbdr_server_config;
+
+VBDR_API int vbdr_server_create(const vbdr_server_config *cfg, vbdr_server_t *out);
+/* Closes every tenant.  Accepts NULL. */
+VBDR_API int vbdr_server_destroy(vbdr_server_t s);
+
+/* Device bytes a tenant holds (state, tables, two staging slots, hosts). */
+VBDR_API uint64_t vbdr_server_tenant_bytes(const vbdr_config *cfg, uint64_t max_pairs,
+                                           uint64_t n_hosts);
+
+/* Admit a tenant with handle configuration cfg, slices of up to max_pairs
+ * pairs and the n_hosts hosts h_aips (host memory, copied) to estimate after
+ * every slice; mlp (may be NULL) adds the learned correction.  Waits up to
+ * timeout_ms for room.  On the fresh state it closes one empty slice (which
+ * changes nothing) before capturing the graphs.
+ * Errors: VBDR_EINVAL, VBDR_ERANGE (larger than the whole budget),
+ * VBDR_ETIMEOUT, VBDR_ENOMEM, VBDR_ECUDA. */
+VBDR_API int vbdr_server_open(vbdr_server_t s, const vbdr_config *cfg, uint64_t max_pairs,
+                              const uint32_t *h_aips, uint64_t n_hosts, vbdr_mlp_t mlp,
+                              uint32_t timeout_ms, uint32_t *tenant);
+/* Release a tenant's memory (after its work finishes) and wake waiters. */
+VBDR_API int vbdr_server_close(vbdr_server_t s, uint32_t tenant);
+
+/* Enqueue one slice of n pairs (h_pairs: host memory, pinned for full copy
+ * speed, valid until the slice's wait returns).  Returns a ticket.
+ * Errors: VBDR_ERANGE (n > max_pairs), VBDR_EORDER (two slices of this tenant
+ * already in flight: wait for one first), VBDR_EINVAL, VBDR_ECUDA. */
+VBDR_API int vbdr_server_submit(vbdr_server_t s, uint32_t tenant, const uint32_t *h_pairs,
+                                uint64_t n, uint64_t *ticket);
+
+/* Wait (host-side polling, bounded by timeout_ms) for a ticket; copy the
+ * slice's estimates into h_out (n_hosts floats, may be NULL).  device_ms: the
+ * graph's execution time; e2e_ms: submit to completion.  Either may be NULL.
+ * Errors: VBDR_EINVAL, VBDR_ETIMEOUT, VBDR_ECUDA. */
+VBDR_API int vbdr_server_wait(vbdr_server_t s, uint32_t tenant, uint64_t ticket, float *h_out,
+                              uint32_t timeout_ms, float *device_ms, float *e2e_ms);
+
+/* Device bytes and tenants currently admitted. */
+VBDR_API int vbdr_server_in_use(vbdr_server_t s, uint64_t *bytes, uint32_t *tenants);
 
 /* ---- inspection (tests, debugging); these synchronise the stream ---- */
 

@@ -12,7 +12,7 @@ library's BF16/FP32 kernels, and the generator of (features, exact
 cardinality) training sets from oracle runs on trace-shaped traffic.
 
 Network: x[80] -> GELU(W1 x + b1)[64] -> GELU(W2 h1 + b2)[64] -> w3 . h2 + b3,
-GELU(z) = z/2 (1 + erf(z / sqrt 2)).  Parameters in a flat float vector laid
+GELU in its tanh form, z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).  Parameters in a flat float vector laid
 out as W1 (64 x 80, row-major), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3 (1).
 """
 from __future__ import annotations
@@ -35,12 +35,24 @@ def unpack(theta: np.ndarray) -> dict:
     return out
 
 
+GELU_A = np.sqrt(2.0 / np.pi)
+GELU_B = 0.044715
+
+
 def gelu(z):
-    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+    """GELU in its tanh form (Hendrycks & Gimpel 2016):
+    z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))."""
+    return 0.5 * z * (1.0 + np.tanh(GELU_A * (z + GELU_B * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+    t = np.tanh(GELU_A * (z + GELU_B * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * GELU_A * (1.0 + 3.0 * GELU_B * z * z)
+
+
+def gelu_exact(z):
+    """z Phi(z), the definition the tanh form approximates."""
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
 
 
 def forward(theta: np.ndarray, X: np.ndarray):

@@ -31,6 +31,8 @@ struct vbdr {
   uint32_t *d_aips;
   float *d_out;
   uint64_t est_cap;
+  uint16_t *d_feat;     // feature rows of the learned estimate [feat_cap][48]
+  uint64_t feat_cap;
 };
 
 namespace {
@@ -104,6 +106,7 @@ void free_state(vbdr *h) {
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   cudaFree(h->d_aips);
   cudaFree(h->d_out);
+  cudaFree(h->d_feat);
 }
 
 }  // namespace
@@ -224,6 +227,16 @@ int vbdr_scan_slice(vbdr_t h, const uint32_t *d_pairs, uint64_t n, void *stream)
   if (!d_pairs || ((uintptr_t)d_pairs & 15u)) return VBDR_EINVAL;
   return fail_cuda(h, vbk::launch_scan(h->d, h->s, h->layout == VBDR_GFAST,
                                         d_pairs, n, (cudaStream_t)stream));
+}
+
+int vbdr_scan_slice_devn(vbdr_t h, const uint32_t *d_pairs, const uint64_t *d_n,
+                         uint64_t max_n, void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (max_n == 0) return VBDR_OK;
+  if (!d_pairs || !d_n || ((uintptr_t)d_pairs & 15u) || ((uintptr_t)d_n & 7u)) return VBDR_EINVAL;
+  return fail_cuda(h, vbk::launch_scan(h->d, h->s, h->layout == VBDR_GFAST, d_pairs, max_n,
+                                       (cudaStream_t)stream, d_n));
 }
 
 int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n, void *stream) {
@@ -356,9 +369,29 @@ int vbdr_estimate_learned(vbdr_t h, vbdr_mlp_t m, const uint32_t *d_aips, uint64
   if (n == 0) return VBDR_OK;
   if (!d_aips || !d_out || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_out & 3u))
     return VBDR_EINVAL;
-  return fail_cuda(h, vbk::launch_estimate_learned(h->d, h->s, h->est, d_aips, n, d_out,
-                                                   (cudaStream_t)stream, h->est_cfg,
-                                                   vbk::mlp_weights(m), vbk::mlp_nmax(m)));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n > h->feat_cap) {
+    // feature rows live in a buffer owned by the handle, grown here (never
+    // inside a graph capture: the service sizes it before capturing)
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    cudaFree(h->d_feat);
+    h->d_feat = nullptr;
+    h->feat_cap = 0;
+    if (cudaMalloc(&h->d_feat, n * vbk::kMlpLive * sizeof(uint16_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return VBDR_ENOMEM;
+    }
+    h->feat_cap = n;
+  }
+  // gather + histogram (plain launch shape) -> feature rows and plain
+  // estimates; then the MLP on the tensor cores corrects them in place
+  cudaError_t e = vbk::launch_features(h->d, h->s, h->est, d_aips, n,
+                                       reinterpret_cast<__nv_bfloat16 *>(h->d_feat), d_out, st,
+                                       h->est_cfg);
+  if (e == cudaSuccess)
+    e = vbk::launch_mlp_correct(m, reinterpret_cast<const __nv_bfloat16 *>(h->d_feat), n, d_out, st);
+  return fail_cuda(h, e);
 }
 
 int vbdr_load_virtual_registers(vbdr_t h, const uint32_t *d_aips, const uint64_t *d_offsets,

@@ -23,7 +23,6 @@
 //            linear-counting decision are computed with the same IEEE
 //            operations as the plain formula, so the decision is exact.
 //            The result is rounded to FP32.
-#include "mlp_device.cuh"
 #include "vbdr_internal.cuh"
 
 namespace vbk {
@@ -31,37 +30,35 @@ namespace {
 
 constexpr int kMaxEstWarps = 16;  // blocks of up to 512 threads
 constexpr int kGatherUnroll = 8;
-constexpr int kLearnedWarps = 4;  // block shape of the feature / learned modes
-
-// What the kernel produces per host.
-enum EstMode { kPlain = 0, kFeatures = 1, kLearned = 2 };
+// What the kernel produces per host: the estimate, or also the learned
+// correction's feature row.
+enum EstMode { kPlain = 0, kFeatures = 1 };
 
 // A warp owns a batch of 32 hosts and splits its lanes into 32/T groups of
 // T lanes; in T steps each group gathers one host of the batch.  The host
 // results land in shared memory so that lane q finishes host q.
-// kFeatures / kLearned also count each host's register values: every lane
-// keeps a private 32-bin byte histogram (a shared-memory row of 36 bytes, so
-// the 32 lanes' rows fall in distinct banks), the group adds its rows per bin
-// and writes bin / g into the batch's BF16 feature tile; the finishing lane
-// adds the noise statistics.  kLearned then runs the MLP on the tile
-// (mma.sync, 32 hosts per warp) and corrects the estimate.
+// kFeatures also counts each host's register values: every lane keeps a
+// private 32-bin byte histogram (a shared-memory row of 36 bytes, so the 32
+// lanes' rows fall in distinct banks; one shared atomic add per value), the
+// group then adds its rows with packed 16-bit SIMD sums (each lane reads 8
+// words), writes bin / g of the feature row, and derives S and V from the
+// bins instead of accumulating them per value.  The finishing lane writes the
+// noise statistics of the row.
 template <bool SMEM_KT, int T, int MODE>  // seed table in shared memory (g_max <= 512)
-__global__ void __launch_bounds__(MODE == kPlain ? kMaxEstWarps * 32 : kLearnedWarps * 32)
+__global__ void __launch_bounds__(kMaxEstWarps * 32)
     estimate_kernel(const uint32_t *__restrict__ aips, uint64_t n,
                     float *__restrict__ out, Dims d, DevState s, EstConst c,
-                    MlpDevWeights mw, float nmax, __nv_bfloat16 *__restrict__ feat_out) {
+                    __nv_bfloat16 *__restrict__ feat_out) {
   static_assert(T == 8 || T == 16 || T == 32, "lanes per host");
   constexpr uint32_t G = 32 / T;  // hosts gathered at once per warp
-  constexpr int WARPS = MODE == kPlain ? kMaxEstWarps : kLearnedWarps;
-  constexpr bool HIST = MODE != kPlain;
+  constexpr int WARPS = kMaxEstWarps;
+  constexpr bool HIST = MODE == kFeatures;
   __shared__ KEnt kt_s[SMEM_KT ? kKtabSize : 1];
   __shared__ double lnv_s[kLnTab];
   __shared__ double nZZ_s;
   __shared__ unsigned long long resS[WARPS][32];
   __shared__ uint32_t resV[WARPS][32];
-  __shared__ uint32_t hrow[HIST ? WARPS : 1][32][9];                    // private histograms
-  __shared__ __align__(16) __nv_bfloat16 ftile[HIST ? WARPS : 1][32][kMlpLive];
-  __shared__ __align__(16) __nv_bfloat16 h1tile[MODE == kLearned ? WARPS : 1][32][kMlpHid];
+  __shared__ uint32_t hrow[HIST ? WARPS : 1][32][9];  // private histograms
   if constexpr (SMEM_KT) {
     const uint32_t gmax = 1u << (d.group_rule ? d.b_min + 3 : d.b);
     for (uint32_t i = threadIdx.x; i < gmax; i += blockDim.x) kt_s[i] = s.ktab[i];
@@ -98,7 +95,7 @@ __global__ void __launch_bounds__(MODE == kPlain ? kMaxEstWarps * 32 : kLearnedW
       uint32_t V = 0;
       if constexpr (HIST) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) hrow[wib][lane][q] = 0u;
+        for (int q = 0; q < 8; ++q) hrow[wib][lane][q] = 0u;
       }
       for (uint32_t base = 0; base < g; base += T * kGatherUnroll) {
         uint32_t M[kGatherUnroll];
@@ -114,29 +111,53 @@ __global__ void __launch_bounds__(MODE == kPlain ? kMaxEstWarps * 32 : kLearnedW
 #pragma unroll
         for (int u = 0; u < kGatherUnroll; ++u) {
           if (M[u] != 0xffu) {
-            S += 1ull << (32u - M[u]);
-            V += (M[u] == 0u);
-            if constexpr (HIST) atomicAdd(&hrow[wib][lane][M[u] >> 2], 1u << (8u * (M[u] & 3u)));
+            if constexpr (HIST) {
+              atomicAdd(&hrow[wib][lane][M[u] >> 2], 1u << (8u * (M[u] & 3u)));
+            } else {
+              S += 1ull << (32u - M[u]);
+              V += (M[u] == 0u);
+            }
           }
         }
       }
       if constexpr (HIST) {
+        // bins 4w..4w+3 (w = sub % 8) summed over the group's rows: 16-bit
+        // fields, bins 4w and 4w+2 in lo, 4w+1 and 4w+3 in hi
         __syncwarp();
-        if (valid) {
-          const float inv_g = 1.0f / (float)g;
+        const uint32_t word = sub & 7u;
+        uint32_t lo = 0, hi = 0;
 #pragma unroll
-          for (uint32_t bb = 0; bb < 32 / T; ++bb) {
-            const uint32_t bin = sub + T * bb;
-            uint32_t cnt = 0;
-            for (uint32_t r = 0; r < T; ++r)
-              cnt += (hrow[wib][grp * T + r][bin >> 2] >> (8u * (bin & 3u))) & 0xffu;
-            ftile[wib][j][bin] = __float2bfloat16((float)cnt * inv_g);
-          }
+        for (uint32_t r = sub >> 3; r < (uint32_t)T; r += T / 8) {
+          const uint32_t v = hrow[wib][grp * T + r][word];
+          lo += v & 0x00ff00ffu;
+          hi += (v >> 8) & 0x00ff00ffu;
         }
+#pragma unroll
+        for (int o = 8; o < T; o <<= 1) {
+          lo += __shfl_xor_sync(0xffffffffu, lo, o, T);
+          hi += __shfl_xor_sync(0xffffffffu, hi, o, T);
+        }
+        const uint32_t c0 = lo & 0xffffu, c1 = hi & 0xffffu, c2 = lo >> 16, c3 = hi >> 16;
+        const uint32_t b0 = 4u * word;
+        if (valid && sub < 8) {
+          const float inv_g = 1.0f / (float)g;
+          __align__(8) __nv_bfloat16 f[4] = {
+              __float2bfloat16((float)c0 * inv_g), __float2bfloat16((float)c1 * inv_g),
+              __float2bfloat16((float)c2 * inv_g), __float2bfloat16((float)c3 * inv_g)};
+          *reinterpret_cast<uint2 *>(feat_out + (hb + j) * kMlpLive + b0) =
+              *reinterpret_cast<const uint2 *>(f);
+        }
+        // S and V from the bins: bin b contributes count * 2^(32 - b); the
+        // 8 lanes sub % 8 = 0..7 of any row subset cover all 32 bins once
+        S = ((unsigned long long)c0 << (32u - b0)) + ((unsigned long long)c1 << (31u - b0)) +
+            ((unsigned long long)c2 << (30u - b0)) + ((unsigned long long)c3 << (29u - b0));
+        S = b0 + 3u <= 32u ? S : 0ull;
+        V = word == 0 ? c0 : 0u;
         __syncwarp();
       }
+      // HIST: every row subset already holds the bin totals -> sum 8 lanes
 #pragma unroll
-      for (int o = T / 2; o > 0; o >>= 1) {
+      for (int o = (HIST ? 4 : T / 2); o > 0; o >>= 1) {
         S += __shfl_xor_sync(0xffffffffu, S, o, T);
         V += __shfl_xor_sync(0xffffffffu, V, o, T);
       }
@@ -159,7 +180,7 @@ __global__ void __launch_bounds__(MODE == kPlain ? kMaxEstWarps * 32 : kLearnedW
       if constexpr (MODE == kPlain) {
         out[h_l] = (float)est;
       } else {
-        __nv_bfloat16 *x = &ftile[wib][lane][32];
+        __align__(16) __nv_bfloat16 x[16];
         x[0] = __float2bfloat16((float)b * 0.0625f);
         x[1] = __float2bfloat16(log1pf((float)est) * 0.0625f);
         x[2] = __float2bfloat16(log1pf((float)n_g) * 0.0625f);
@@ -168,28 +189,10 @@ __global__ void __launch_bounds__(MODE == kPlain ? kMaxEstWarps * 32 : kLearnedW
         x[5] = __float2bfloat16((float)myV / (float)(1u << b));
 #pragma unroll
         for (int q = 6; q < 16; ++q) x[q] = __float2bfloat16(0.f);
-        resS[wib][lane] = __double_as_longlong(est);
-      }
-    }
-    if constexpr (MODE == kFeatures) {
-      __syncwarp();
-      for (uint32_t i = lane; i < 32 * kMlpLive; i += 32) {
-        const uint64_t r = hb + i / kMlpLive;
-        if (r < n) feat_out[r * kMlpLive + i % kMlpLive] = ftile[wib][i / kMlpLive][i % kMlpLive];
-      }
-      if (h_l < n) out[h_l] = (float)__longlong_as_double(resS[wib][lane]);
-    } else if constexpr (MODE == kLearned) {
-      __syncwarp();
-      if (h_l >= n) {  // rows past the end: defined inputs for the tensor cores
-        for (int q = 0; q < kMlpLive; ++q) ftile[wib][lane][q] = __float2bfloat16(0.f);
-      }
-      __syncwarp();
-      const float delta = mlp_forward_warp(&ftile[wib][0][0], &h1tile[wib][0][0], mw);
-      if (h_l < n) {
-        const float plain = (float)__longlong_as_double(resS[wib][lane]);
-        float corr = expm1f(log1pf(plain) + delta);
-        if (!(corr > 0.f)) corr = 0.f;
-        out[h_l] = plain > nmax ? plain : corr;
+        uint4 *dst = reinterpret_cast<uint4 *>(feat_out + h_l * kMlpLive + 32);
+        dst[0] = *reinterpret_cast<const uint4 *>(&x[0]);
+        dst[1] = *reinterpret_cast<const uint4 *>(&x[8]);
+        out[h_l] = (float)est;
       }
     }
     __syncwarp();
@@ -207,10 +210,10 @@ void *estimate_kernel_ptr(int T) {
 
 template <int MODE>
 cudaError_t launch_mode(const Dims &d, const DevState &s, const EstConst &c, const uint32_t *aips,
-                        uint64_t n, float *out, cudaStream_t st, EstLaunch cfg, MlpDevWeights mw,
-                        float nmax, __nv_bfloat16 *feat) {
+                        uint64_t n, float *out, cudaStream_t st, EstLaunch cfg,
+                        __nv_bfloat16 *feat) {
   if (n == 0) return cudaSuccess;
-  const int threads = MODE == kPlain ? cfg.threads : kLearnedWarps * 32;
+  const int threads = cfg.threads;
   if (threads < 32 || threads > kMaxEstWarps * 32 || threads % 32) return cudaErrorInvalidValue;
   const bool smem_kt = (1u << (d.group_rule ? d.b_min + 3 : d.b)) <= (uint32_t)kKtabSize;
   void *kern = smem_kt ? estimate_kernel_ptr<true, MODE>(cfg.lanes)
@@ -224,8 +227,8 @@ cudaError_t launch_mode(const Dims &d, const DevState &s, const EstConst &c, con
   const uint64_t want = (n + hosts_per_block - 1) / hosts_per_block;
   uint64_t grid = (uint64_t)sms * per_sm;  // persistent: one wave, grid-stride
   if (want < grid) grid = want;
-  void *args[] = {(void *)&aips, (void *)&n, (void *)&out, (void *)&d, (void *)&s,
-                  (void *)&c,    (void *)&mw, (void *)&nmax, (void *)&feat};
+  void *args[] = {(void *)&aips, (void *)&n, (void *)&out, (void *)&d,
+                  (void *)&s,    (void *)&c, (void *)&feat};
   return cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(threads), args, 0, st);
 }
 
@@ -238,19 +241,13 @@ const EstLaunch kEstCandidates[kNumEstCandidates] = {
 cudaError_t launch_estimate(const Dims &d, const DevState &s, const EstConst &c,
                             const uint32_t *aips, uint64_t n, float *out,
                             cudaStream_t st, EstLaunch cfg) {
-  return launch_mode<kPlain>(d, s, c, aips, n, out, st, cfg, MlpDevWeights{}, 0.f, nullptr);
+  return launch_mode<kPlain>(d, s, c, aips, n, out, st, cfg, nullptr);
 }
 
 cudaError_t launch_features(const Dims &d, const DevState &s, const EstConst &c,
                             const uint32_t *aips, uint64_t n, __nv_bfloat16 *feat, float *plain,
                             cudaStream_t st, EstLaunch cfg) {
-  return launch_mode<kFeatures>(d, s, c, aips, n, plain, st, cfg, MlpDevWeights{}, 0.f, feat);
-}
-
-cudaError_t launch_estimate_learned(const Dims &d, const DevState &s, const EstConst &c,
-                                    const uint32_t *aips, uint64_t n, float *out, cudaStream_t st,
-                                    EstLaunch cfg, MlpDevWeights mw, float nmax) {
-  return launch_mode<kLearned>(d, s, c, aips, n, out, st, cfg, mw, nmax, nullptr);
+  return launch_mode<kFeatures>(d, s, c, aips, n, plain, st, cfg, feat);
 }
 
 }  // namespace vbk

@@ -23,6 +23,7 @@ struct vbdr_mlp {
   float *adam_m, *adam_v;
   __nv_bfloat16 *w1c;    // [64][48]
   __nv_bfloat16 *w2;     // [64][64]
+  uint2 *w1f, *w2f;      // BF16 weights in mma fragment order (inference)
   float *loss;           // [2]: sum of squared errors, samples
   float nmax;            // plain estimates above this fall back uncorrected
   uint64_t step;
@@ -308,33 +309,104 @@ __global__ void adamw_kernel(float *theta, float *grad, float *m, float *v,
   }
 }
 
-// BF16 copies of W1 (live columns) and W2 from the master.
-__global__ void refresh_bf16_kernel(const float *theta, __nv_bfloat16 *w1c, __nv_bfloat16 *w2) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpHid * kMlpLive;
-       i += gridDim.x * blockDim.x)
-    w1c[i] = __float2bfloat16(theta[kOffW1 + (i / kMlpLive) * kMlpIn + w1_col(i % kMlpLive)]);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpHid * kMlpHid;
-       i += gridDim.x * blockDim.x)
-    w2[i] = __float2bfloat16(theta[kOffW2 + i]);
+__device__ __forceinline__ uint32_t pack_rn(float lo, float hi) {
+  return pack_bf16(__float2bfloat16(lo), __float2bfloat16(hi));
 }
 
-__global__ void __launch_bounds__(128)
+// BF16 copies of W1 (live columns) and W2 from the master, row-major for the
+// training kernel and in mma fragment order for inference.
+__global__ void refresh_bf16_kernel(const float *theta, __nv_bfloat16 *w1c, __nv_bfloat16 *w2,
+                                    uint2 *w1f, uint2 *w2f) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int i = tid; i < kMlpHid * kMlpLive; i += nth)
+    w1c[i] = __float2bfloat16(theta[kOffW1 + (i / kMlpLive) * kMlpIn + w1_col(i % kMlpLive)]);
+  for (int i = tid; i < kMlpHid * kMlpHid; i += nth) w2[i] = __float2bfloat16(theta[kOffW2 + i]);
+  // fragment entry e = (kk * 8 + n) * 32 + lane: B[k][j] = W[8n + j][16kk + k]
+  for (int e = tid; e < kW1Frags + kW2Frags; e += nth) {
+    const bool l1 = e < kW1Frags;
+    const int f = l1 ? e : e - kW1Frags;
+    const int lane = f & 31, n = (f >> 5) & 7, kk = f >> 8;
+    const int row = 8 * n + (lane >> 2), k0 = 16 * kk + 2 * (lane & 3);
+    auto W = [&](int k) {
+      return l1 ? theta[kOffW1 + row * kMlpIn + w1_col(k)] : theta[kOffW2 + row * kMlpHid + k];
+    };
+    const uint2 v = make_uint2(pack_rn(W(k0), W(k0 + 1)), pack_rn(W(k0 + 8), W(k0 + 9)));
+    if (l1) w1f[f] = v; else w2f[f] = v;
+  }
+}
+
+// One warp per 32 rows: copy the rows' features into a padded shared tile
+// (16-byte chunks), run the network; optional correction of est in place.
+__device__ __forceinline__ void stage_rows(const __nv_bfloat16 *X, uint64_t n, uint64_t r0,
+                                           __nv_bfloat16 *xs) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t rows = n - r0 < 32 ? n - r0 : 32;
+  const uint4 *src = reinterpret_cast<const uint4 *>(X + r0 * kMlpLive);
+  for (int i = lane; i < 32 * (kMlpLive / 8); i += 32) {
+    const int r = i / (kMlpLive / 8), q = i % (kMlpLive / 8);
+    *reinterpret_cast<uint4 *>(xs + r * kXLd + 8 * q) =
+        (uint64_t)r < rows ? src[i] : make_uint4(0, 0, 0, 0);
+  }
+  __syncwarp();
+}
+
+template <int WARPS>
+__device__ __forceinline__ MlpDevWeights stage_weights(const MlpDevWeights &w, uint2 *w1s,
+                                                       uint2 *w2s, float *bs) {
+  for (int i = threadIdx.x; i < kW1Frags; i += WARPS * 32) w1s[i] = w.w1f[i];
+  for (int i = threadIdx.x; i < kW2Frags; i += WARPS * 32) w2s[i] = w.w2f[i];
+  for (int i = threadIdx.x; i < kMlpHid; i += WARPS * 32) {
+    bs[i] = w.b1[i];
+    bs[kMlpHid + i] = w.b2[i];
+    bs[2 * kMlpHid + i] = w.w3[i];
+  }
+  if (threadIdx.x == 0) bs[3 * kMlpHid] = *w.b3;
+  __syncthreads();
+  return MlpDevWeights{w1s, w2s, bs, bs + kMlpHid, bs + 2 * kMlpHid, bs + 3 * kMlpHid};
+}
+
+constexpr int kFwdWarps = 4;  // 46 KB of static shared memory per block
+
+__global__ void __launch_bounds__(kFwdWarps * 32)
     forward_kernel(const __nv_bfloat16 *__restrict__ X, uint64_t n, MlpDevWeights w,
                    float *__restrict__ delta) {
-  __shared__ __align__(16) __nv_bfloat16 xs[4][32][kMlpLive];
-  __shared__ __align__(16) __nv_bfloat16 h1s[4][32][kMlpHid];
+  __shared__ uint2 w1s[kW1Frags], w2s[kW2Frags];
+  __shared__ float bs[3 * kMlpHid + 1];
+  __shared__ __align__(16) __nv_bfloat16 xs[kFwdWarps][32 * kXLd];
+  __shared__ __align__(16) __nv_bfloat16 h1s[kFwdWarps][32 * kHLd];
+  const MlpDevWeights ws = stage_weights<kFwdWarps>(w, w1s, w2s, bs);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t warps = (uint64_t)gridDim.x * 4;
-  for (uint64_t r0 = ((uint64_t)blockIdx.x * 4 + warp) * 32; r0 < n; r0 += warps * 32) {
-    for (int i = lane; i < 32 * kMlpLive; i += 32) {
-      const uint64_t r = r0 + i / kMlpLive;
-      xs[warp][i / kMlpLive][i % kMlpLive] =
-          r < n ? X[r * kMlpLive + i % kMlpLive] : __float2bfloat16(0.f);
-    }
-    __syncwarp();
-    const float d = mlp_forward_warp(&xs[warp][0][0], &h1s[warp][0][0], w);
+  const uint64_t warps = (uint64_t)gridDim.x * kFwdWarps;
+  for (uint64_t r0 = ((uint64_t)blockIdx.x * kFwdWarps + warp) * 32; r0 < n; r0 += warps * 32) {
+    stage_rows(X, n, r0, xs[warp]);
+    const float d = mlp_forward_warp(xs[warp], h1s[warp], ws);
     if (r0 + lane < n) delta[r0 + lane] = d;
-    __syncwarp();
+  }
+}
+
+// Learned correction of plain estimates from feature rows: weights staged in
+// shared memory once per block, then 32 hosts per warp on the tensor cores;
+// est[i] (the plain estimate) is replaced by the corrected one unless it
+// exceeds nmax.
+__global__ void __launch_bounds__(kFwdWarps * 32)
+    correct_kernel(const __nv_bfloat16 *__restrict__ X, uint64_t n, MlpDevWeights w, float nmax,
+                   float *__restrict__ est) {
+  __shared__ uint2 w1s[kW1Frags], w2s[kW2Frags];
+  __shared__ float bs[3 * kMlpHid + 1];
+  __shared__ __align__(16) __nv_bfloat16 xs[kFwdWarps][32 * kXLd];
+  __shared__ __align__(16) __nv_bfloat16 h1s[kFwdWarps][32 * kHLd];
+  const MlpDevWeights ws = stage_weights<kFwdWarps>(w, w1s, w2s, bs);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t warps = (uint64_t)gridDim.x * kFwdWarps;
+  for (uint64_t r0 = ((uint64_t)blockIdx.x * kFwdWarps + warp) * 32; r0 < n; r0 += warps * 32) {
+    stage_rows(X, n, r0, xs[warp]);
+    const float d = mlp_forward_warp(xs[warp], h1s[warp], ws);
+    if (r0 + lane < n) {
+      const float plain = est[r0 + lane];
+      float corr = expm1f(log1pf(plain) + d);
+      if (!(corr > 0.f)) corr = 0.f;
+      est[r0 + lane] = plain > nmax ? plain : corr;
+    }
   }
 }
 
@@ -385,6 +457,8 @@ int vbdr_mlp_create(uint64_t seed, vbdr_mlp_t *out) {
   if (e == cudaSuccess) e = cudaMalloc(&m->w1c, kMlpHid * kMlpLive * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->w2, kMlpHid * kMlpHid * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->loss, 2 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->w1f, kW1Frags * sizeof(uint2));
+  if (e == cudaSuccess) e = cudaMalloc(&m->w2f, kW2Frags * sizeof(uint2));
   if (e != cudaSuccess) {
     cudaGetLastError();
     vbdr_mlp_destroy(m);
@@ -426,6 +500,8 @@ int vbdr_mlp_destroy(vbdr_mlp_t m) {
   cudaFree(m->w1c);
   cudaFree(m->w2);
   cudaFree(m->loss);
+  cudaFree(m->w1f);
+  cudaFree(m->w2f);
   delete m;
   return VBDR_OK;
 }
@@ -438,7 +514,7 @@ int vbdr_mlp_set_params(vbdr_mlp_t m, const float *h_params, float nmax) {
   if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, kMlpParams * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, kMlpParams * sizeof(float));
   if (e == cudaSuccess) {
-    refresh_bf16_kernel<<<64, 256>>>(m->theta, m->w1c, m->w2);
+    refresh_bf16_kernel<<<64, 256>>>(m->theta, m->w1c, m->w2, m->w1f, m->w2f);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -514,7 +590,7 @@ int vbdr_mlp_train(vbdr_mlp_t m, const uint16_t *d_X, const float *d_y, uint64_t
                                        weight_decay, b1, b2, eps, bc1, bc2);
       e = cudaGetLastError();
       if (e == cudaSuccess) {
-        refresh_bf16_kernel<<<16, 256, 0, st>>>(m->theta, m->w1c, m->w2);
+        refresh_bf16_kernel<<<16, 256, 0, st>>>(m->theta, m->w1c, m->w2, m->w1f, m->w2f);
         e = cudaGetLastError();
       }
     }
@@ -533,8 +609,8 @@ int vbdr_mlp_forward(vbdr_mlp_t m, const uint16_t *d_X, uint64_t n, float *d_del
   if (m->sticky) return m->sticky;
   if (n == 0) return VBDR_OK;
   if (!d_X || !d_delta) return VBDR_EINVAL;
-  MlpDevWeights w{m->w1c, m->w2, m->theta};
-  forward_kernel<<<grid_of((n + 31) / 32, 4), 128, 0, (cudaStream_t)stream>>>(
+  MlpDevWeights w = mlp_weights(m);
+  forward_kernel<<<grid_of((n + 31) / 32, kFwdWarps), kFwdWarps * 32, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const __nv_bfloat16 *>(d_X), n, w, d_delta);
   return mlp_fail(m, cudaGetLastError());
 }
@@ -542,6 +618,17 @@ int vbdr_mlp_forward(vbdr_mlp_t m, const uint16_t *d_X, uint64_t n, float *d_del
 }  // extern "C"
 
 namespace vbk {
-MlpDevWeights mlp_weights(const vbdr_mlp *m) { return MlpDevWeights{m->w1c, m->w2, m->theta}; }
+cudaError_t launch_mlp_correct(const vbdr_mlp *m, const __nv_bfloat16 *X, uint64_t n, float *est,
+                               cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  correct_kernel<<<grid_of((n + 31) / 32, kFwdWarps), kFwdWarps * 32, 0, st>>>(X, n, mlp_weights(m),
+                                                                              m->nmax, est);
+  return cudaGetLastError();
+}
+
+MlpDevWeights mlp_weights(const vbdr_mlp *m) {
+  return MlpDevWeights{m->w1f, m->w2f, m->theta + kOffB1, m->theta + kOffB2, m->theta + kOffW3,
+                       m->theta + kOffB3};
+}
 float mlp_nmax(const vbdr_mlp *m) { return m->nmax; }
 }  // namespace vbk

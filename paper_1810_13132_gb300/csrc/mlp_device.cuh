@@ -2,7 +2,8 @@
 //
 // The correction (not part of the paper) maps a host's feature vector to a
 // log-space correction delta of the plain estimate:
-//   x[80] -> GELU(W1 x + b1)[64] -> GELU(W2 h1 + b2)[64] -> w3 . h2 + b3.
+//   x[80] -> GELU(W1 x + b1)[64] -> GELU(W2 h1 + b2)[64] -> w3 . h2 + b3,
+// GELU in its tanh form.
 // Feature definition (80 inputs): x[v] = #{registers with value v} / g for
 // v = 0..63, x[64] = b/16, x[65] = ln(1 + n_plain)/16, x[66] = ln(1 + n_g)/16,
 // x[67] = ln(1 + n_Z/Z), x[68] = V_Z/Z, x[69] = V/g, x[70..79] = 0.
@@ -37,21 +38,57 @@ constexpr int kMlpParams = kOffB3 + 1;
 // Column of W1 (80-input layout) holding live input k (0..47).
 __host__ __device__ __forceinline__ int w1_col(int k) { return k < 32 ? k : k + 32; }
 
-// BF16 copies of the weights in the layouts the kernels read:
-//   w1c[n][k] = W1[n][w1_col(k)]  (64 x 48),  w2[n][j] = W2[n][j]  (64 x 64)
+// BF16 weights in mma fragment order: for k-step kk and 8-column tile n, lane
+// L's B fragment of W^T (two 32-bit words) is w1f[(kk * 8 + n) * 32 + L], so
+// a warp reads a whole fragment with one conflict-free 8-byte load per lane.
+//   layer 1: B[k][j] = W1[8n + j][w1_col(16kk + k)],  kk < 3
+//   layer 2: B[k][j] = W2[8n + j][16kk + k],          kk < 4
+constexpr int kW1Frags = (kMlpLive / 16) * 8 * 32;  // uint2 entries
+constexpr int kW2Frags = (kMlpHid / 16) * 8 * 32;
 struct MlpDevWeights {
-  const __nv_bfloat16 *w1c;
-  const __nv_bfloat16 *w2;
-  const float *theta;  // FP32 master (biases and w3 are read from here)
+  const uint2 *w1f;
+  const uint2 *w2f;
+  const float *b1, *b2, *w3, *b3;  // FP32 (global, or staged in shared memory)
 };
+// Padded row strides (elements) of the per-warp input and hidden tiles: 56 and
+// 72 BF16 (28 and 36 words) put the 8 rows of a fragment in distinct banks.
+constexpr int kXLd = 56;
+constexpr int kHLd = 72;
+
+// GELU in its tanh form, z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))),
+// with the hardware tanh approximation (tanh.approx.f32).
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+constexpr float kGeluA = 0.7978845608028654f;  // sqrt(2/pi)
+constexpr float kGeluB = 0.044715f;
 
 __device__ __forceinline__ float gelu_f(float z) {
-  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+  const float t = tanh_fast(kGeluA * z * (1.0f + kGeluB * z * z));
+  return 0.5f * z * (1.0f + t);
+}
+
+__device__ __forceinline__ __nv_bfloat162 tanh_fast2(__nv_bfloat162 x) {
+  uint32_t y;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(*reinterpret_cast<uint32_t *>(&x)));
+  return *reinterpret_cast<__nv_bfloat162 *>(&y);
+}
+
+// GELU (tanh form) of a BF16 pair in BF16 arithmetic.
+__device__ __forceinline__ __nv_bfloat162 gelu_bf16x2(__nv_bfloat162 z) {
+  const __nv_bfloat162 a = __float2bfloat162_rn(kGeluA), b = __float2bfloat162_rn(kGeluB);
+  const __nv_bfloat162 one = __float2bfloat162_rn(1.0f), half = __float2bfloat162_rn(0.5f);
+  const __nv_bfloat162 u = __hmul2(__hmul2(a, z), __hfma2(__hmul2(b, z), z, one));
+  const __nv_bfloat162 t = tanh_fast2(u);
+  return __hmul2(__hmul2(half, z), __hadd2(one, t));
 }
 
 __device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
-         z * __expf(-0.5f * z * z) * 0.39894228040143268f;
+  const float t = tanh_fast(kGeluA * z * (1.0f + kGeluB * z * z));
+  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * kGeluA * (1.0f + 3.0f * kGeluB * z * z);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
@@ -89,14 +126,23 @@ __device__ __forceinline__ void load_b(uint32_t (&b)[2], BT bt) {
   b[1] = pack_bf16(bt(c + 8, g), bt(c + 9, g));
 }
 
+// A fragment of a row-major BF16 tile (leading dimension ld elements) whose
+// top-left corner is t: pairs of consecutive columns read as 32-bit words.
+__device__ __forceinline__ void load_a_tile(uint32_t (&a)[4], const __nv_bfloat16 *t, int ld) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, c = (lane & 3) * 2;
+  a[0] = *reinterpret_cast<const uint32_t *>(t + g * ld + c);
+  a[1] = *reinterpret_cast<const uint32_t *>(t + (g + 8) * ld + c);
+  a[2] = *reinterpret_cast<const uint32_t *>(t + g * ld + c + 8);
+  a[3] = *reinterpret_cast<const uint32_t *>(t + (g + 8) * ld + c + 8);
+}
+
 // Forward of 32 rows by one warp.  xs: the rows' live inputs, BF16
-// [32][kMlpLive]; h1s: scratch BF16 [32][kMlpHid] (may alias nothing else).
+// [32][kXLd] (first kMlpLive columns used); h1s: scratch BF16 [32][kHLd].
 // Returns delta of row (lane) in every lane.  z2 / h2 stay in registers.
 __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
                                                   __nv_bfloat16 *h1s,
                                                   const MlpDevWeights &w) {
   const int lane = threadIdx.x & 31, g = lane >> 2, c = (lane & 3) * 2;
-  // layer 1: [32 x 48] x [48 x 64]
   float acc[2][8][4];
 #pragma unroll
   for (int m = 0; m < 2; ++m)
@@ -104,29 +150,32 @@ __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
     for (int n = 0; n < 8; ++n)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.f;
+  // layer 1: [32 x 48] x [48 x 64]
 #pragma unroll
   for (int kk = 0; kk < kMlpLive / 16; ++kk) {
     uint32_t a[2][4];
 #pragma unroll
-    for (int m = 0; m < 2; ++m)
-      load_a(a[m], [&](int r, int k) { return xs[(16 * m + r) * kMlpLive + 16 * kk + k]; });
+    for (int m = 0; m < 2; ++m) load_a_tile(a[m], xs + 16 * m * kXLd + 16 * kk, kXLd);
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-      uint32_t b[2];
-      load_b(b, [&](int k, int j) { return w.w1c[(8 * n + j) * kMlpLive + 16 * kk + k]; });
+      const uint2 f = w.w1f[(kk * 8 + n) * 32 + lane];
+      const uint32_t b[2] = {f.x, f.y};
 #pragma unroll
       for (int m = 0; m < 2; ++m) mma_bf16(acc[m][n], a[m], b);
     }
   }
-  // bias + GELU -> h1 (BF16) in shared memory
+  // bias + GELU -> h1 (BF16) in shared memory; h1 is BF16 anyway, so the
+  // GELU of this layer runs on packed BF16 pairs
 #pragma unroll
   for (int m = 0; m < 2; ++m)
 #pragma unroll
     for (int n = 0; n < 8; ++n)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = 16 * m + g + (q >> 1) * 8, j = 8 * n + c + (q & 1);
-        h1s[r * kMlpHid + j] = __float2bfloat16(gelu_f(acc[m][n][q] + w.theta[kOffB1 + j]));
+      for (int h = 0; h < 2; ++h) {
+        const int r = 16 * m + g + 8 * h, j = 8 * n + c;
+        const __nv_bfloat162 z = __floats2bfloat162_rn(acc[m][n][2 * h] + w.b1[j],
+                                                       acc[m][n][2 * h + 1] + w.b1[j + 1]);
+        *reinterpret_cast<__nv_bfloat162 *>(h1s + r * kHLd + j) = gelu_bf16x2(z);
       }
   __syncwarp();
   // layer 2: [32 x 64] x [64 x 64]
@@ -140,12 +189,11 @@ __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
   for (int kk = 0; kk < kMlpHid / 16; ++kk) {
     uint32_t a[2][4];
 #pragma unroll
-    for (int m = 0; m < 2; ++m)
-      load_a(a[m], [&](int r, int k) { return h1s[(16 * m + r) * kMlpHid + 16 * kk + k]; });
+    for (int m = 0; m < 2; ++m) load_a_tile(a[m], h1s + 16 * m * kHLd + 16 * kk, kHLd);
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-      uint32_t b[2];
-      load_b(b, [&](int k, int j) { return w.w2[(8 * n + j) * kMlpHid + 16 * kk + k]; });
+      const uint2 f = w.w2f[(kk * 8 + n) * 32 + lane];
+      const uint32_t b[2] = {f.x, f.y};
 #pragma unroll
       for (int m = 0; m < 2; ++m) mma_bf16(acc[m][n], a[m], b);
     }
@@ -159,7 +207,7 @@ __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int j = 8 * n + c + (q & 1);
-        part[2 * m + (q >> 1)] += gelu_f(acc[m][n][q] + w.theta[kOffB2 + j]) * w.theta[kOffW3 + j];
+        part[2 * m + (q >> 1)] += gelu_f(acc[m][n][q] + w.b2[j]) * w.w3[j];
       }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -175,7 +223,7 @@ __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
   const int slot = lane >> 3;
   const float delta = slot == 0 ? d0 : slot == 1 ? d1 : slot == 2 ? d2 : d3;
   __syncwarp();
-  return delta + w.theta[kOffB3];
+  return delta + *w.b3;
 }
 
 }  // namespace vbk

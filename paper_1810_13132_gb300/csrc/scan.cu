@@ -81,7 +81,11 @@ __device__ __forceinline__ void pair_update(const Dims &d, const KEnt *kt, uint3
 // and read with shared-memory loads; otherwise it is read from global memory.
 template <int W, bool MIXED, bool SMEM_KT>  // W = 0: gfast; W = DR width: gsmall
 __global__ void __launch_bounds__(kScanThreads)
-    scan_kernel(const uint4 *__restrict__ pairs2, uint64_t n_pairs, Dims d, DevState s) {
+    scan_kernel(const uint4 *__restrict__ pairs2, uint64_t n_pairs, const uint64_t *n_dev,
+                Dims d, DevState s) {
+  // n_dev: the slice size read from device memory (a graph replayed for
+  // slices of any size up to n_pairs); otherwise n_pairs is the size.
+  if (n_dev) n_pairs = min(*n_dev, n_pairs);
   __shared__ KEnt kt_s[SMEM_KT ? kKtabSize : 1];
   const KEnt *kt;
   if constexpr (SMEM_KT) {
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(kScanThreads)
 
 template <int W, bool MIXED>
 cudaError_t launch_scan_t(const Dims &d, const DevState &s, const uint32_t *pairs, uint64_t n,
-                          cudaStream_t st) {
+                          const uint64_t *n_dev, cudaStream_t st) {
   const bool smem_kt = (1u << (MIXED ? d.b_min + 3 : d.b)) <= (uint32_t)kKtabSize;
   auto kern = smem_kt ? scan_kernel<W, MIXED, true> : scan_kernel<W, MIXED, false>;
   int dev = 0, sms = 0, per_sm = 0;
@@ -158,23 +162,24 @@ cudaError_t launch_scan_t(const Dims &d, const DevState &s, const uint32_t *pair
   const uint64_t want = (units + kScanThreads - 1) / kScanThreads;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (want < grid) grid = want ? want : 1;
-  kern<<<(unsigned)grid, kScanThreads, 0, st>>>(reinterpret_cast<const uint4 *>(pairs), n, d, s);
+  kern<<<(unsigned)grid, kScanThreads, 0, st>>>(reinterpret_cast<const uint4 *>(pairs), n, n_dev,
+                                                d, s);
   return cudaGetLastError();
 }
 
 template <bool MIXED>
 cudaError_t launch_scan_m(const Dims &d, const DevState &s, bool gfast, const uint32_t *pairs,
-                          uint64_t n, cudaStream_t st) {
-  if (gfast) return launch_scan_t<0, MIXED>(d, s, pairs, n, st);
+                          uint64_t n, const uint64_t *n_dev, cudaStream_t st) {
+  if (gfast) return launch_scan_t<0, MIXED>(d, s, pairs, n, n_dev, st);
   switch (d.w) {
-    case 1: return launch_scan_t<1, MIXED>(d, s, pairs, n, st);
-    case 2: return launch_scan_t<2, MIXED>(d, s, pairs, n, st);
-    case 3: return launch_scan_t<3, MIXED>(d, s, pairs, n, st);
-    case 4: return launch_scan_t<4, MIXED>(d, s, pairs, n, st);
-    case 5: return launch_scan_t<5, MIXED>(d, s, pairs, n, st);
-    case 6: return launch_scan_t<6, MIXED>(d, s, pairs, n, st);
-    case 7: return launch_scan_t<7, MIXED>(d, s, pairs, n, st);
-    case 8: return launch_scan_t<8, MIXED>(d, s, pairs, n, st);
+    case 1: return launch_scan_t<1, MIXED>(d, s, pairs, n, n_dev, st);
+    case 2: return launch_scan_t<2, MIXED>(d, s, pairs, n, n_dev, st);
+    case 3: return launch_scan_t<3, MIXED>(d, s, pairs, n, n_dev, st);
+    case 4: return launch_scan_t<4, MIXED>(d, s, pairs, n, n_dev, st);
+    case 5: return launch_scan_t<5, MIXED>(d, s, pairs, n, n_dev, st);
+    case 6: return launch_scan_t<6, MIXED>(d, s, pairs, n, n_dev, st);
+    case 7: return launch_scan_t<7, MIXED>(d, s, pairs, n, n_dev, st);
+    case 8: return launch_scan_t<8, MIXED>(d, s, pairs, n, n_dev, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -182,10 +187,10 @@ cudaError_t launch_scan_m(const Dims &d, const DevState &s, bool gfast, const ui
 }  // namespace
 
 cudaError_t launch_scan(const Dims &d, const DevState &s, bool gfast, const uint32_t *pairs,
-                        uint64_t n, cudaStream_t st) {
+                        uint64_t n, cudaStream_t st, const uint64_t *n_dev) {
   if (n == 0) return cudaSuccess;
-  return d.group_rule ? launch_scan_m<true>(d, s, gfast, pairs, n, st)
-                      : launch_scan_m<false>(d, s, gfast, pairs, n, st);
+  return d.group_rule ? launch_scan_m<true>(d, s, gfast, pairs, n, n_dev, st)
+                      : launch_scan_m<false>(d, s, gfast, pairs, n, n_dev, st);
 }
 
 }  // namespace vbk

@@ -126,7 +126,8 @@ __device__ __forceinline__ uint32_t host_b(const Dims &d, uint32_t aip) {
 // ----- launchers (defined in the kernel translation units) -----
 cudaError_t launch_init(const Dims &d, const DevState &s, cudaStream_t st);
 cudaError_t launch_scan(const Dims &d, const DevState &s, bool gfast,
-                        const uint32_t *pairs, uint64_t n, cudaStream_t st);
+                        const uint32_t *pairs, uint64_t n, cudaStream_t st,
+                        const uint64_t *n_dev = nullptr);
 cudaError_t launch_slide(const Dims &d, const DevState &s, bool gfast,
                          cudaStream_t st);
 // Launch shape of the estimate kernel: lanes cooperating on one host and
@@ -145,10 +146,9 @@ cudaError_t launch_estimate(const Dims &d, const DevState &s, const EstConst &c,
 cudaError_t launch_features(const Dims &d, const DevState &s, const EstConst &c,
                             const uint32_t *aips, uint64_t n, __nv_bfloat16 *feat, float *plain,
                             cudaStream_t st, EstLaunch cfg);
-cudaError_t launch_estimate_learned(const Dims &d, const DevState &s, const EstConst &c,
-                                    const uint32_t *aips, uint64_t n, float *out, cudaStream_t st,
-                                    EstLaunch cfg, MlpDevWeights mw, float nmax);
 MlpDevWeights mlp_weights(const vbdr_mlp *m);
+cudaError_t launch_mlp_correct(const vbdr_mlp *m, const __nv_bfloat16 *X, uint64_t n, float *est,
+                               cudaStream_t st);
 float mlp_nmax(const vbdr_mlp *m);
 cudaError_t launch_load_virtual(const Dims &d, const DevState &s, const uint32_t *aips,
                                 const uint64_t *offsets, uint64_t n, const uint8_t *vregs,

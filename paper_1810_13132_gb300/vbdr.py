@@ -67,6 +67,18 @@ _SIGS = {
     "vbdr_mlp_forward": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
     "vbdr_features": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP, _VP]),
     "vbdr_estimate_learned": (ctypes.c_int, [_VP, _VP, _VP, _U64, _VP, _VP]),
+    "vbdr_scan_slice_devn": (ctypes.c_int, [_VP, _VP, _VP, _U64, _VP]),
+    "vbdr_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_VP)]),
+    "vbdr_server_destroy": (ctypes.c_int, [_VP]),
+    "vbdr_server_tenant_bytes": (_U64, [ctypes.POINTER(vbdr_config), _U64, _U64]),
+    "vbdr_server_open": (ctypes.c_int, [_VP, ctypes.POINTER(vbdr_config), _U64, _VP, _U64, _VP,
+                                        _U32, ctypes.POINTER(_U32)]),
+    "vbdr_server_close": (ctypes.c_int, [_VP, _U32]),
+    "vbdr_server_submit": (ctypes.c_int, [_VP, _U32, _VP, _U64, ctypes.POINTER(_U64)]),
+    "vbdr_server_wait": (ctypes.c_int, [_VP, _U32, _U64, _VP, _U32,
+                                        ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_float)]),
+    "vbdr_server_in_use": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U32)]),
     "vbdr_estimate_registers_noalloc": (ctypes.c_int, [_VP, _U64, _U32, _U64, _VP, _U64, _VP,
                                                        _VP]),
 }
@@ -265,6 +277,76 @@ class Vbdr:
         _check("vbdr_copy_pool_sums", self._L.vbdr_copy_pool_sums(
             self._h, ctypes.byref(S), ctypes.byref(V), _stream_ptr(stream)))
         return S.value, V.value
+
+
+class server_config(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("max_tenants", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class Server:
+    """Streaming service (see include/vbdr.h): tenants admitted under a device
+    memory budget, one CUDA graph replay per slice."""
+
+    def __init__(self, budget_bytes: int, max_tenants: int = 16):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the service needs a CUDA GPU")
+        torch.cuda.init()
+        self._L = load()
+        h = ctypes.c_void_p()
+        c = server_config(budget_bytes, max_tenants, 0)
+        _check("vbdr_server_create", self._L.vbdr_server_create(ctypes.byref(c), ctypes.byref(h)))
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._L.vbdr_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tenant_bytes(self, cfg: Config, max_pairs: int, n_hosts: int) -> int:
+        c = cfg.to_c()
+        return self._L.vbdr_server_tenant_bytes(ctypes.byref(c), max_pairs, n_hosts)
+
+    def open(self, cfg: Config, max_pairs: int, aips: np.ndarray, mlp: "Mlp | None" = None,
+             timeout_ms: int = 60000) -> int:
+        aips = np.ascontiguousarray(aips, dtype=np.uint32)
+        c = cfg.to_c()
+        t = ctypes.c_uint32()
+        _check("vbdr_server_open", self._L.vbdr_server_open(
+            self._h, ctypes.byref(c), max_pairs, aips.ctypes.data, aips.size,
+            mlp._h if mlp is not None else None, timeout_ms, ctypes.byref(t)))
+        return t.value
+
+    def close_tenant(self, tenant: int) -> None:
+        _check("vbdr_server_close", self._L.vbdr_server_close(self._h, tenant))
+
+    def submit(self, tenant: int, pairs) -> int:
+        ptr, n = _host_ptr(pairs, 2)
+        tk = ctypes.c_uint64()
+        _check("vbdr_server_submit", self._L.vbdr_server_submit(self._h, tenant, ptr, n,
+                                                                ctypes.byref(tk)))
+        return tk.value
+
+    def wait(self, tenant: int, ticket: int, out: np.ndarray | None = None,
+             timeout_ms: int = 60000) -> tuple[float, float]:
+        dms, ems = ctypes.c_float(), ctypes.c_float()
+        _check("vbdr_server_wait", self._L.vbdr_server_wait(
+            self._h, tenant, ticket, out.ctypes.data if out is not None else None, timeout_ms,
+            ctypes.byref(dms), ctypes.byref(ems)))
+        return dms.value, ems.value
+
+    def in_use(self) -> tuple[int, int]:
+        b, t = ctypes.c_uint64(), ctypes.c_uint32()
+        _check("vbdr_server_in_use", self._L.vbdr_server_in_use(self._h, ctypes.byref(b),
+                                                                ctypes.byref(t)))
+        return b.value, t.value
 
 
 class Mlp:

@@ -154,3 +154,52 @@ SMALL = dict(name="small k=10 N=1e5 H=1000 Z=2^16 g=128", k=10, n_pairs=100_000,
 TRACE = dict(name="trace k=30 N=64M H=1M Z=2^24 g=256", k=30, n_pairs=64 << 20,
              n_hosts=1_000_000, zipf_s=1.05, c_max=2_000_000, Z=1 << 24, log2_g=8,
              repeat_frac=0.10)
+
+
+class StreamingTraffic:
+    """Traffic of the streaming-service workload: host ranks Zipf(s) over
+    n_hosts active hosts (drawn by inverting the continuous rank-size law,
+    O(1) per pair), bips uniform 32-bit, plus bursty superspreaders -- a
+    fraction `spreader_frac` of the hosts, each active in bursts of 1..5
+    slices with probability `burst_p` per slice, emitting about
+    `spreader_pairs` fresh bips per active slice.
+
+    make_pool(n) returns one (n, 2) uint32 block; a slice of size N is a
+    window of a pool block.
+    """
+
+    def __init__(self, n_hosts: int, zipf_s: float, seed: int, spreader_frac: float = 1e-4,
+                 burst_p: float = 0.05, spreader_pairs: int = 100_000):
+        self.rng = np.random.default_rng(seed)
+        self.n_hosts, self.s = n_hosts, zipf_s
+        self.aips = distinct_u32(self.rng, n_hosts)
+        n_sp = max(1, int(round(n_hosts * spreader_frac)))
+        self.spreaders = self.aips[self.rng.choice(n_hosts, n_sp, replace=False)]
+        self.burst_p, self.spreader_pairs = burst_p, spreader_pairs
+        self.burst_left = np.zeros(n_sp, dtype=np.int64)
+
+    def _ranks(self, n: int) -> np.ndarray:
+        a = 1.0 - self.s
+        u = self.rng.random(n)
+        r = np.floor((u * (self.n_hosts ** a - 1.0) + 1.0) ** (1.0 / a)).astype(np.int64)
+        return np.clip(r, 1, self.n_hosts) - 1
+
+    def make_pool(self, n: int) -> np.ndarray:
+        out = np.empty((n, 2), dtype=U32)
+        # superspreader bursts: start with probability burst_p, last 1..5 slices
+        start = (self.burst_left == 0) & (self.rng.random(self.spreaders.size) < self.burst_p)
+        self.burst_left[start] = self.rng.integers(1, 6, size=int(start.sum()))
+        active = self.spreaders[self.burst_left > 0]
+        self.burst_left = np.maximum(self.burst_left - 1, 0)
+        n_sp = min(n // 2, active.size * self.spreader_pairs)
+        n_bg = n - n_sp
+        out[:n_bg, 0] = self.aips[self._ranks(n_bg)]
+        if n_sp:
+            out[n_bg:, 0] = np.repeat(active, self.spreader_pairs)[:n_sp]
+        out[:, 1] = self.rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(U32)
+        out[:] = out[self.rng.permutation(n)] if n <= (1 << 22) else out
+        return out
+
+
+STREAM = dict(name="stream N~logU[1M,128M] H=8M Z=2^26 g=256 k=30", k=30, n_lo=1 << 20,
+              n_hi=128 << 20, n_hosts=8_000_000, zipf_s=1.1, Z=1 << 26, log2_g=8)
