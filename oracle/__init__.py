@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
                                          u64p, u64p, u64p, u32p]
         L.orc_get_state.argtypes = [ctypes.c_void_p, u8p, u32p, u8p, u8p]
         L.orc_set_registers.argtypes = [ctypes.c_void_p, u8p]
+        L.orc_set_state.argtypes = [ctypes.c_void_p, u8p, u32p]
         L.orc_pool_sums_get.argtypes = [ctypes.c_void_p, u64p, u64p]
         L.orc_features.restype = ctypes.c_int
         L.orc_features.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, f64p, f64p]
@@ -228,6 +229,12 @@ class Oracle:
         reg = np.empty(self.Z, dtype=np.uint8)
         lib().orc_get_state(self._h, None, None, _ptr(reg, ctypes.c_uint8), None)
         return reg
+
+    def set_state(self, dr: np.ndarray | None = None, bs: np.ndarray | None = None) -> None:
+        d = None if dr is None else np.ascontiguousarray(dr, dtype=np.uint8)
+        b = None if bs is None else np.ascontiguousarray(bs, dtype=np.uint32)
+        lib().orc_set_state(self._h, None if d is None else _ptr(d, ctypes.c_uint8),
+                            None if b is None else _ptr(b, ctypes.c_uint32))
 
     def set_registers(self, reg: np.ndarray) -> None:
         reg = np.ascontiguousarray(reg, dtype=np.uint8)

@@ -392,6 +392,16 @@ void orc_get_state(const orc_t *o, uint8_t *dr_out, uint32_t *bs_out,
   }
 }
 
+/* Overwrite the logical DRV ([Z][R], entries 1..R) and bsLBP1 ([Z]); either
+ * pointer may be NULL.  Used to install a state merged from several
+ * replicas that each scanned part of a slice. */
+void orc_set_state(orc_t *o, const uint8_t *dr_in, const uint32_t *bs_in) {
+  for (uint64_t j = 0; j < o->Z; ++j) {
+    if (dr_in) memcpy(o->DR + j * (o->R + 1) + 1, dr_in + j * o->R, o->R);
+    if (bs_in) o->bs[j] = bs_in[j];
+  }
+}
+
 /* Overwrite the register array and recompute the pool sums: used to put a
  * register-level synthetic state (one whose scan would be too long to run)
  * under the estimator. */
