@@ -38,7 +38,7 @@ def _args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--layout", default="gfast", choices=["gfast", "gsmall"])
+    p.add_argument("--layout", default="gfast", choices=["gfast", "gsmall", "serial"])
     p.add_argument("--workload", default="trace", choices=["trace", "small", "batched", "serve"])
     p.add_argument("--tenants", type=int, default=2, help="serve: concurrent tenants")
     p.add_argument("--slices-per-tenant", type=int, default=40, help="serve: timed slices")
@@ -314,7 +314,9 @@ def run_ours(a):
     peak, peak_kind = _peaks()
     Z, P = wl["Z"], v.words
     scan_bytes = 8 * N
-    slide_bytes = Z * ((4 * P + 4) + (4 * P + 4 + 1)) if a.layout == "gfast" else Z * (4 * P + 4 * P + 1)
+    slide_bytes = {"gfast": Z * ((4 * P + 4) + (4 * P + 4 + 1)),   # DRV + bsLBP1 in, DRV + bsLBP1 + reg out
+                   "gsmall": Z * (4 * P + 4 * P + 1),               # DRV in, DRV + reg out
+                   "serial": Z * ((4 * P + 1) + (4 * P + 1 + 1))}[a.layout]  # DRV + nowLBP1
     est_bytes = H * (4 + 4) + Z
     kern = {"scan": (statistics.mean(scan_ms), scan_bytes),
             "slide": (statistics.mean(slide_ms), slide_bytes),

@@ -67,8 +67,12 @@ typedef enum {
  *                (Alg. 7), the slide folds the highest set bit (Alg. 6).
  *   VBDR_GSMALL: DRV only; the scan zeroes a DR in place (Alg. 9), the slide
  *                ages every DR (Alg. 8).  Smaller state, random RMW of the
- *                DRV during the scan.                                       */
-typedef enum { VBDR_GFAST = 0, VBDR_GSMALL = 1 } vbdr_layout;
+ *                DRV during the scan.
+ *   VBDR_SERIAL: DRV plus one nowLBP1 byte (Alg. 1 / 4): the scan raises
+ *                nowLBP1 to the pair's LBP1 with a byte-wise atomic max (the
+ *                race of Sec. 4.2 cannot lose the larger value), the slide
+ *                folds it like Alg. 6.  Same DRV as gfast after every slide.*/
+typedef enum { VBDR_GFAST = 0, VBDR_GSMALL = 1, VBDR_SERIAL = 2 } vbdr_layout;
 
 typedef struct {
   uint32_t k;          /* slices per window, 1..255                         */
@@ -339,8 +343,8 @@ VBDR_API int vbdr_get_dims(vbdr_t h, uint32_t *R, uint32_t *w, uint32_t *words);
 
 /* Copy the logical state to host memory (any pointer may be NULL):
  * h_dr [Z][R] uint8 (DR of LBP1 value r+1 at [j][r]), h_bs [Z] uint32
- * (gfast bsLBP1; zeros for gsmall), h_reg [Z] uint8 registers of the last
- * slide. */
+ * (gfast: bsLBP1; serial: nowLBP1; gsmall: zeros), h_reg [Z] uint8 registers
+ * of the last slide. */
 VBDR_API int vbdr_copy_state(vbdr_t h, uint8_t *h_dr, uint32_t *h_bs, uint8_t *h_reg,
                     void *stream);
 

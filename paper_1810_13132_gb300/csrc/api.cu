@@ -94,6 +94,7 @@ uint32_t ktab_entries(const Dims &d) {
 void free_state(vbdr *h) {
   cudaFree(h->s.drv);
   cudaFree(h->s.bs);
+  cudaFree(h->s.now);
   cudaFree(h->s.reg);
   cudaFree(h->s.ktab);
   cudaFree(h->s.lnv);
@@ -131,7 +132,8 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   *out = nullptr;
   if (!cfg || cfg->reserved != 0) return VBDR_EINVAL;
   if (cfg->k < 1 || cfg->k > 255) return VBDR_EINVAL;
-  if (cfg->layout != VBDR_GFAST && cfg->layout != VBDR_GSMALL) return VBDR_EINVAL;
+  if (cfg->layout != VBDR_GFAST && cfg->layout != VBDR_GSMALL && cfg->layout != VBDR_SERIAL)
+    return VBDR_EINVAL;
   if (cfg->group_rule > 1) return VBDR_EINVAL;
   const uint32_t b_min = cfg->log2_g_min ? cfg->log2_g_min : cfg->log2_g;
   if (b_min < 1 || b_min > (uint32_t)vbk::kMaxLog2G) return VBDR_EINVAL;
@@ -174,6 +176,10 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   e = cudaMalloc(&h->s.drv, (size_t)d.P * d.Zs * sizeof(uint32_t));
   if (e == cudaSuccess && h->layout == VBDR_GFAST)
     e = cudaMalloc(&h->s.bs, (size_t)d.Z * sizeof(uint32_t));
+  if (e == cudaSuccess && h->layout == VBDR_SERIAL) {
+    e = cudaMalloc(&h->s.now, (size_t)d.Zs);
+    if (e == cudaSuccess) e = cudaMemset(h->s.now, 0, (size_t)d.Zs);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&h->s.reg, (size_t)d.Zs);  // whole 32-bit words
   if (e == cudaSuccess) e = cudaMalloc(&h->s.ktab, (size_t)kn * sizeof(vbk::KEnt));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.lnv, vbk::kLnTab * sizeof(double));
@@ -225,7 +231,7 @@ int vbdr_scan_slice(vbdr_t h, const uint32_t *d_pairs, uint64_t n, void *stream)
   if (h->sticky) return h->sticky;
   if (n == 0) return VBDR_OK;
   if (!d_pairs || ((uintptr_t)d_pairs & 15u)) return VBDR_EINVAL;
-  return fail_cuda(h, vbk::launch_scan(h->d, h->s, h->layout == VBDR_GFAST,
+  return fail_cuda(h, vbk::launch_scan(h->d, h->s, h->layout,
                                         d_pairs, n, (cudaStream_t)stream));
 }
 
@@ -235,7 +241,7 @@ int vbdr_scan_slice_devn(vbdr_t h, const uint32_t *d_pairs, const uint64_t *d_n,
   if (h->sticky) return h->sticky;
   if (max_n == 0) return VBDR_OK;
   if (!d_pairs || !d_n || ((uintptr_t)d_pairs & 15u) || ((uintptr_t)d_n & 7u)) return VBDR_EINVAL;
-  return fail_cuda(h, vbk::launch_scan(h->d, h->s, h->layout == VBDR_GFAST, d_pairs, max_n,
+  return fail_cuda(h, vbk::launch_scan(h->d, h->s, h->layout, d_pairs, max_n,
                                        (cudaStream_t)stream, d_n));
 }
 
@@ -282,7 +288,7 @@ int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n, void *st
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[buf], h->copy_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_copied[buf], 0);
     if (e != cudaSuccess) return fail_cuda(h, e);
-    e = vbk::launch_scan(h->d, h->s, h->layout == VBDR_GFAST, h->stage[buf], cnt, st);
+    e = vbk::launch_scan(h->d, h->s, h->layout, h->stage[buf], cnt, st);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_free[buf], st);
     if (e != cudaSuccess) return fail_cuda(h, e);
     done += cnt;
@@ -294,7 +300,7 @@ int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n, void *st
 int vbdr_slide(vbdr_t h, void *stream) {
   if (!h) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
-  int rc = fail_cuda(h, vbk::launch_slide(h->d, h->s, h->layout == VBDR_GFAST,
+  int rc = fail_cuda(h, vbk::launch_slide(h->d, h->s, h->layout,
                                            (cudaStream_t)stream));
   if (rc == VBDR_OK) h->slid = true;
   return rc;
@@ -482,10 +488,15 @@ int vbdr_copy_state(vbdr_t h, uint8_t *h_dr, uint32_t *h_bs, uint8_t *h_reg,
       }
   }
   if (h_bs) {
-    if (h->s.bs)
+    if (h->s.bs) {
       e = cudaMemcpy(h_bs, h->s.bs, d.Z * 4, cudaMemcpyDeviceToHost);
-    else
+    } else if (h->s.now) {  // serial: nowLBP1 values
+      std::vector<uint8_t> now(d.Z);
+      e = cudaMemcpy(now.data(), h->s.now, d.Z, cudaMemcpyDeviceToHost);
+      for (uint64_t j = 0; j < d.Z; ++j) h_bs[j] = now[j];
+    } else {
       std::memset(h_bs, 0, d.Z * 4);
+    }
     if (e != cudaSuccess) return fail_cuda(h, e);
   }
   if (h_reg) {

@@ -136,90 +136,84 @@ __device__ __forceinline__ void load_a_tile(uint32_t (&a)[4], const __nv_bfloat1
   a[3] = *reinterpret_cast<const uint32_t *>(t + (g + 8) * ld + c + 8);
 }
 
-// Forward of 32 rows by one warp.  xs: the rows' live inputs, BF16
-// [32][kXLd] (first kMlpLive columns used); h1s: scratch BF16 [32][kHLd].
-// Returns delta of row (lane) in every lane.  z2 / h2 stay in registers.
+// Forward of 32 rows by one warp, one 16-row tile at a time (32 FP32
+// accumulators live instead of 64, for occupancy).  xs: the rows' live
+// inputs, BF16 [32][kXLd] (first kMlpLive columns used); h1s: scratch BF16
+// [32][kHLd].  Returns delta of row (lane) in every lane.
 __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
                                                   __nv_bfloat16 *h1s,
                                                   const MlpDevWeights &w) {
   const int lane = threadIdx.x & 31, g = lane >> 2, c = (lane & 3) * 2;
-  float acc[2][8][4];
-#pragma unroll
-  for (int m = 0; m < 2; ++m)
+  float part[2][2];  // [tile][row g / g+8]
+#pragma unroll 1
+  for (int m = 0; m < 2; ++m) {
+    float acc[8][4];
 #pragma unroll
     for (int n = 0; n < 8; ++n)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.f;
-  // layer 1: [32 x 48] x [48 x 64]
+      for (int q = 0; q < 4; ++q) acc[n][q] = 0.f;
+    // layer 1: [16 x 48] x [48 x 64]
 #pragma unroll
-  for (int kk = 0; kk < kMlpLive / 16; ++kk) {
-    uint32_t a[2][4];
+    for (int kk = 0; kk < kMlpLive / 16; ++kk) {
+      uint32_t a[4];
+      load_a_tile(a, xs + 16 * m * kXLd + 16 * kk, kXLd);
 #pragma unroll
-    for (int m = 0; m < 2; ++m) load_a_tile(a[m], xs + 16 * m * kXLd + 16 * kk, kXLd);
-#pragma unroll
-    for (int n = 0; n < 8; ++n) {
-      const uint2 f = w.w1f[(kk * 8 + n) * 32 + lane];
-      const uint32_t b[2] = {f.x, f.y};
-#pragma unroll
-      for (int m = 0; m < 2; ++m) mma_bf16(acc[m][n], a[m], b);
+      for (int n = 0; n < 8; ++n) {
+        const uint2 f = w.w1f[(kk * 8 + n) * 32 + lane];
+        const uint32_t b[2] = {f.x, f.y};
+        mma_bf16(acc[n], a, b);
+      }
     }
-  }
-  // bias + GELU -> h1 (BF16) in shared memory; h1 is BF16 anyway, so the
-  // GELU of this layer runs on packed BF16 pairs
-#pragma unroll
-  for (int m = 0; m < 2; ++m)
+    // bias + GELU -> h1 (BF16; its GELU runs on packed BF16 pairs)
 #pragma unroll
     for (int n = 0; n < 8; ++n)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int r = 16 * m + g + 8 * h, j = 8 * n + c;
-        const __nv_bfloat162 z = __floats2bfloat162_rn(acc[m][n][2 * h] + w.b1[j],
-                                                       acc[m][n][2 * h + 1] + w.b1[j + 1]);
+        const __nv_bfloat162 z = __floats2bfloat162_rn(acc[n][2 * h] + w.b1[j],
+                                                       acc[n][2 * h + 1] + w.b1[j + 1]);
         *reinterpret_cast<__nv_bfloat162 *>(h1s + r * kHLd + j) = gelu_bf16x2(z);
       }
-  __syncwarp();
-  // layer 2: [32 x 64] x [64 x 64]
-#pragma unroll
-  for (int m = 0; m < 2; ++m)
+    __syncwarp();
+    // layer 2: [16 x 64] x [64 x 64]
 #pragma unroll
     for (int n = 0; n < 8; ++n)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.f;
+      for (int q = 0; q < 4; ++q) acc[n][q] = 0.f;
 #pragma unroll
-  for (int kk = 0; kk < kMlpHid / 16; ++kk) {
-    uint32_t a[2][4];
+    for (int kk = 0; kk < kMlpHid / 16; ++kk) {
+      uint32_t a[4];
+      load_a_tile(a, h1s + 16 * m * kHLd + 16 * kk, kHLd);
 #pragma unroll
-    for (int m = 0; m < 2; ++m) load_a_tile(a[m], h1s + 16 * m * kHLd + 16 * kk, kHLd);
-#pragma unroll
-    for (int n = 0; n < 8; ++n) {
-      const uint2 f = w.w2f[(kk * 8 + n) * 32 + lane];
-      const uint32_t b[2] = {f.x, f.y};
-#pragma unroll
-      for (int m = 0; m < 2; ++m) mma_bf16(acc[m][n], a[m], b);
+      for (int n = 0; n < 8; ++n) {
+        const uint2 f = w.w2f[(kk * 8 + n) * 32 + lane];
+        const uint32_t b[2] = {f.x, f.y};
+        mma_bf16(acc[n], a, b);
+      }
     }
-  }
-  // output layer in FP32: delta_r = sum_j GELU(z2[r][j]) w3[j] + b3
-  float part[4] = {0.f, 0.f, 0.f, 0.f};  // rows g, g+8, 16+g, 24+g
-#pragma unroll
-  for (int m = 0; m < 2; ++m)
+    // output layer in FP32: delta_r = sum_j GELU(z2[r][j]) w3[j] + b3
+    part[m][0] = part[m][1] = 0.f;
 #pragma unroll
     for (int n = 0; n < 8; ++n)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int j = 8 * n + c + (q & 1);
-        part[2 * m + (q >> 1)] += gelu_f(acc[m][n][q] + w.b2[j]) * w.w3[j];
+        part[m][q >> 1] += gelu_f(acc[n][q] + w.b2[j]) * w.w3[j];
       }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    part[i] += __shfl_xor_sync(0xffffffffu, part[i], 1);
-    part[i] += __shfl_xor_sync(0xffffffffu, part[i], 2);
   }
-  // row r lives in lanes 4*(r % 8) .. +3, slot (r / 8)
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      part[m][h] += __shfl_xor_sync(0xffffffffu, part[m][h], 1);
+      part[m][h] += __shfl_xor_sync(0xffffffffu, part[m][h], 2);
+    }
+  // row r lives in lanes 4*(r % 8) .. +3: tile r / 16, half (r / 8) % 2
   const int src = 4 * (lane & 7);
-  const float d0 = __shfl_sync(0xffffffffu, part[0], src);
-  const float d1 = __shfl_sync(0xffffffffu, part[1], src);
-  const float d2 = __shfl_sync(0xffffffffu, part[2], src);
-  const float d3 = __shfl_sync(0xffffffffu, part[3], src);
+  const float d0 = __shfl_sync(0xffffffffu, part[0][0], src);
+  const float d1 = __shfl_sync(0xffffffffu, part[0][1], src);
+  const float d2 = __shfl_sync(0xffffffffu, part[1][0], src);
+  const float d3 = __shfl_sync(0xffffffffu, part[1][1], src);
   const int slot = lane >> 3;
   const float delta = slot == 0 ? d0 : slot == 1 ? d1 : slot == 2 ? d2 : d3;
   __syncwarp();

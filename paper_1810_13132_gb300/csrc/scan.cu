@@ -1,13 +1,17 @@
-// scan.cu -- per-slice IP-pair scan (Sec. 4.2): Alg. 7 (gfast) and Alg. 9
-// (gsmall), with the per-pair steps of Alg. 4 and Alg. 3.
+// scan.cu -- per-slice IP-pair scan (Sec. 4.2): Alg. 7 (gfast), Alg. 9
+// (gsmall) and Alg. 4's nowLBP1 maximum (serial layout, made safe for
+// parallel threads by a byte-wise atomic max), with the per-pair steps of
+// Alg. 4 and Alg. 3.
 //
 // Per pair:
 //   bip' = H(bip, 2^32, A1); vidx = left b bits of bip'; x = bip' << b;
 //   LBP1 = min(clz(x) + 1, 32 - b); pidx = H(aip, Z, H(vidx, 2^32, A0)).
 // The update is idempotent and monotone during a scan -- gfast ORs bit
 // LBP1-1 into bsLBP1[pidx] (Alg. 7), gsmall zeroes the DR of LBP1 in the DRV
-// of pidx (Alg. 9) -- so the state after the scan does not depend on thread
-// order, and an update whose effect is already visible can be dropped.
+// of pidx (Alg. 9), serial raises nowLBP1[pidx] to LBP1 (Alg. 4; Sec. 4.2's
+// race, a lost larger value, cannot happen with an atomic max) -- so the
+// state after the scan does not depend on thread order, and an update whose
+// effect is already visible can be dropped.
 //
 // Design (measured on GB300, see the design notes):
 //   * streaming: 16-byte loads of two pairs (L1::no_allocate), UNROLL loads
@@ -57,6 +61,7 @@ __device__ __forceinline__ void red_and(uint32_t *p, uint32_t v) {
 // Target word offset and update mask of one pair.
 //   gfast : word = pidx (bsLBP1), mask = the bit to set
 //   gsmall: word = plane * Zs + pidx (DRV), mask = the field bits to clear
+//   serial: word = pidx (byte of nowLBP1), mask = LBP1 (the value to max in)
 template <int W, bool MIXED>
 __device__ __forceinline__ void pair_update(const Dims &d, const KEnt *kt, uint32_t aip,
                                             uint32_t bip, uint64_t &word, uint32_t &mask) {
@@ -69,6 +74,9 @@ __device__ __forceinline__ void pair_update(const Dims &d, const KEnt *kt, uint3
   if constexpr (W == 0) {
     word = pidx;
     mask = 1u << r0;
+  } else if constexpr (W < 0) {
+    word = pidx;
+    mask = r0 + 1u;
   } else {
     constexpr uint32_t F = 32 / W;
     constexpr uint32_t FM = (1u << W) - 1u;
@@ -79,7 +87,19 @@ __device__ __forceinline__ void pair_update(const Dims &d, const KEnt *kt, uint3
 
 // SMEM_KT: the seed table (g_max <= 512 entries) is staged in shared memory
 // and read with shared-memory loads; otherwise it is read from global memory.
-template <int W, bool MIXED, bool SMEM_KT>  // W = 0: gfast; W = DR width: gsmall
+// Byte-wise max into nowLBP1 through a CAS on its 32-bit word.  A failed
+// CAS means another thread raised that word (at most 4 * 31 times), so the
+// loop ends; the iteration cap is a second guard.
+__device__ __forceinline__ void byte_max(uint32_t *w, uint32_t sh, uint32_t v, uint32_t old) {
+  for (int it = 0; it < 256 && ((old >> sh) & 0xffu) < v; ++it) {
+    const uint32_t seen = atomicCAS(w, old, (old & ~(0xffu << sh)) | (v << sh));
+    if (seen == old) break;
+    old = seen;
+  }
+}
+
+// W = 0: gfast; W = DR width: gsmall; W = -1: serial (nowLBP1 bytes)
+template <int W, bool MIXED, bool SMEM_KT>
 __global__ void __launch_bounds__(kScanThreads)
     scan_kernel(const uint4 *__restrict__ pairs2, uint64_t n_pairs, const uint64_t *n_dev,
                 Dims d, DevState s) {
@@ -96,7 +116,7 @@ __global__ void __launch_bounds__(kScanThreads)
   } else {
     kt = s.ktab;
   }
-  uint32_t *const state = (W == 0) ? s.bs : s.drv;
+  uint32_t *const state = (W == 0) ? s.bs : (W < 0 ? reinterpret_cast<uint32_t *>(s.now) : s.drv);
 
   const uint64_t units = n_pairs >> 1;  // whole 16-byte loads
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -118,18 +138,26 @@ __global__ void __launch_bounds__(kScanThreads)
       if (!ok) mask[2 * u] = mask[2 * u + 1] = 0u;
       // adjacent pairs of one load on the same word: one update
       if (word[2 * u] == word[2 * u + 1]) {
-        mask[2 * u] |= mask[2 * u + 1];
+        mask[2 * u] = W < 0 ? max(mask[2 * u], mask[2 * u + 1]) : (mask[2 * u] | mask[2 * u + 1]);
         mask[2 * u + 1] = 0u;
       }
     }
     uint32_t old[2 * kUnroll];
 #pragma unroll
-    for (int q = 0; q < 2 * kUnroll; ++q)
-      old[q] = mask[q] ? ld_ca(state + word[q]) : (W == 0 ? 0xffffffffu : 0u);
+    for (int q = 0; q < 2 * kUnroll; ++q) {
+      const uint64_t wi = W < 0 ? word[q] >> 2 : word[q];
+      // serial: the update is a CAS that waits for its answer, so a stale L1
+      // copy costs a round trip; read the current word from L2 instead
+      old[q] = mask[q] ? (W < 0 ? __ldcg(state + wi) : ld_ca(state + wi))
+                       : (W == 0 ? 0xffffffffu : 0u);
+    }
 #pragma unroll
     for (int q = 0; q < 2 * kUnroll; ++q) {
       if constexpr (W == 0) {
         if (~old[q] & mask[q]) red_or(state + word[q], mask[q]);
+      } else if constexpr (W < 0) {
+        const uint32_t sh = 8u * (uint32_t)(word[q] & 3u);
+        if (((old[q] >> sh) & 0xffu) < mask[q]) byte_max(state + (word[q] >> 2), sh, mask[q], old[q]);
       } else {
         if (old[q] & mask[q]) red_and(state + word[q], ~mask[q]);
       }
@@ -143,6 +171,8 @@ __global__ void __launch_bounds__(kScanThreads)
     pair_update<W, MIXED>(d, kt, p[0], p[1], word, mask);
     if constexpr (W == 0)
       red_or(state + word, mask);
+    else if constexpr (W < 0)
+      byte_max(state + (word >> 2), 8u * (uint32_t)(word & 3u), mask, state[word >> 2]);
     else
       red_and(state + word, ~mask);
   }
@@ -168,9 +198,10 @@ cudaError_t launch_scan_t(const Dims &d, const DevState &s, const uint32_t *pair
 }
 
 template <bool MIXED>
-cudaError_t launch_scan_m(const Dims &d, const DevState &s, bool gfast, const uint32_t *pairs,
+cudaError_t launch_scan_m(const Dims &d, const DevState &s, int layout, const uint32_t *pairs,
                           uint64_t n, const uint64_t *n_dev, cudaStream_t st) {
-  if (gfast) return launch_scan_t<0, MIXED>(d, s, pairs, n, n_dev, st);
+  if (layout == kLayoutGfast) return launch_scan_t<0, MIXED>(d, s, pairs, n, n_dev, st);
+  if (layout == kLayoutSerial) return launch_scan_t<-1, MIXED>(d, s, pairs, n, n_dev, st);
   switch (d.w) {
     case 1: return launch_scan_t<1, MIXED>(d, s, pairs, n, n_dev, st);
     case 2: return launch_scan_t<2, MIXED>(d, s, pairs, n, n_dev, st);
@@ -186,11 +217,11 @@ cudaError_t launch_scan_m(const Dims &d, const DevState &s, bool gfast, const ui
 
 }  // namespace
 
-cudaError_t launch_scan(const Dims &d, const DevState &s, bool gfast, const uint32_t *pairs,
+cudaError_t launch_scan(const Dims &d, const DevState &s, int layout, const uint32_t *pairs,
                         uint64_t n, cudaStream_t st, const uint64_t *n_dev) {
   if (n == 0) return cudaSuccess;
-  return d.group_rule ? launch_scan_m<true>(d, s, gfast, pairs, n, n_dev, st)
-                      : launch_scan_m<false>(d, s, gfast, pairs, n, n_dev, st);
+  return d.group_rule ? launch_scan_m<true>(d, s, layout, pairs, n, n_dev, st)
+                      : launch_scan_m<false>(d, s, layout, pairs, n, n_dev, st);
 }
 
 }  // namespace vbk

@@ -127,7 +127,8 @@ uint64_t vbdr_server_tenant_bytes(const vbdr_config *cfg, uint64_t max_pairs, ui
   const uint32_t b_min = cfg->log2_g_min ? cfg->log2_g_min : cfg->log2_g;
   const uint32_t R = 32 - b_min, F = 32 / w, P = (R + F - 1) / F;
   const uint64_t Zs = (cfg->num_bdr + 3) & ~3ull;
-  uint64_t bytes = Zs * (4ull * P + 1) + (cfg->layout == VBDR_GFAST ? 4 * cfg->num_bdr : 0);
+  uint64_t bytes = Zs * (4ull * P + 1) + (cfg->layout == VBDR_GFAST ? 4 * cfg->num_bdr : 0) +
+                   (cfg->layout == VBDR_SERIAL ? Zs : 0);
   bytes += 64ull << 10;                                // tables, sums
   bytes += 2 * (max_pairs * 8 + 8 + n_hosts * 4);      // staging slots
   bytes += n_hosts * 4;                                // host list

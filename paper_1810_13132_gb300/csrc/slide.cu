@@ -3,6 +3,8 @@
 //   gfast : Alg. 6 -- every DR slides (saturating +1), the DR of the highest
 //           set bit of bsLBP1 is set to 0, bsLBP1 is cleared; then Alg. 2
 //           reads the register (largest LBP1 whose DR is below k, else 0).
+//   serial: Alg. 1 -- the same with nowLBP1 (the slice's largest LBP1)
+//           instead of the highest bit of bsLBP1; nowLBP1 is cleared.
 //   gsmall: Alg. 2 reads the register of the window that just closed, then
 //           Alg. 8 slides every DR for the next slice.
 // Fused into the same pass: the register array and the pool sums
@@ -127,9 +129,11 @@ __device__ __forceinline__ void set_comp(uint4 &v, int c, uint32_t x) {
   if (c == 0) v.x = x; else if (c == 1) v.y = x; else if (c == 2) v.z = x; else v.w = x;
 }
 
-template <int W, int P, bool GFAST>
+// LAY: kLayoutGfast / kLayoutGsmall / kLayoutSerial
+template <int W, int P, int LAY>
 __global__ void __launch_bounds__(kSlideThreads)
     slide_kernel(Dims d, DevState s, uint32_t krep_even) {
+  constexpr bool GFAST = LAY != kLayoutGsmall;  // fold a slice maximum (Alg. 1 / 6)
   unsigned long long S = 0, V = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -141,7 +145,18 @@ __global__ void __launch_bounds__(kSlideThreads)
     for (int p = 0; p < P; ++p)
       v[p] = __ldcs(reinterpret_cast<const uint4 *>(s.drv + (uint64_t)p * d.Zs + j));
     uint4 bsq = make_uint4(0, 0, 0, 0);
-    if constexpr (GFAST) bsq = __ldcs(reinterpret_cast<const uint4 *>(s.bs + j));
+    if constexpr (LAY == kLayoutGfast) bsq = __ldcs(reinterpret_cast<const uint4 *>(s.bs + j));
+    if constexpr (LAY == kLayoutSerial) {
+      // nowLBP1 of the 4 BDRs as the bit of that LBP1, so Alg. 1 and Alg. 6
+      // share the fold
+      const uint32_t nw = __ldcs(reinterpret_cast<const uint32_t *>(s.now + j));
+      bsq = make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t nv = (nw >> (8 * c)) & 0xffu;
+        set_comp(bsq, c, nv ? 1u << (nv - 1u) : 0u);
+      }
+    }
     uint32_t regs = 0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -158,9 +173,12 @@ __global__ void __launch_bounds__(kSlideThreads)
 #pragma unroll
     for (int p = 0; p < P; ++p)
       __stcs(reinterpret_cast<uint4 *>(s.drv + (uint64_t)p * d.Zs + j), v[p]);
-    if constexpr (GFAST) {
+    if constexpr (LAY == kLayoutGfast) {
       if (bsq.x | bsq.y | bsq.z | bsq.w)
         __stcs(reinterpret_cast<uint4 *>(s.bs + j), make_uint4(0, 0, 0, 0));
+    }
+    if constexpr (LAY == kLayoutSerial) {
+      if (bsq.x | bsq.y | bsq.z | bsq.w) __stcs(reinterpret_cast<uint32_t *>(s.now + j), 0u);
     }
     __stcs(reinterpret_cast<uint32_t *>(s.reg + j), regs);
   }
@@ -170,11 +188,14 @@ __global__ void __launch_bounds__(kSlideThreads)
     uint32_t w[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) w[p] = s.drv[(uint64_t)p * d.Zs + j];
-    const uint32_t bsv = GFAST ? s.bs[j] : 0u;
+    uint32_t bsv = 0u;
+    if constexpr (LAY == kLayoutGfast) bsv = s.bs[j];
+    if constexpr (LAY == kLayoutSerial) bsv = s.now[j] ? 1u << (s.now[j] - 1u) : 0u;
     const uint32_t reg = slide_one<W, P, GFAST>(w, bsv, krep_even);
 #pragma unroll
     for (int p = 0; p < P; ++p) s.drv[(uint64_t)p * d.Zs + j] = w[p];
-    if (GFAST && bsv) s.bs[j] = 0u;
+    if (LAY == kLayoutGfast && bsv) s.bs[j] = 0u;
+    if (LAY == kLayoutSerial && bsv) s.now[j] = 0u;
     s.reg[j] = (uint8_t)reg;
     S += 1ull << (32u - reg);
     V += (reg == 0u);
@@ -206,15 +227,12 @@ __global__ void __launch_bounds__(kSlideThreads)
   }
 }
 
-template <int W, int P>
-cudaError_t launch_slide_t(const Dims &d, const DevState &s, bool gfast, cudaStream_t st) {
+template <int W, int P, int LAY>
+cudaError_t launch_slide_l(const Dims &d, const DevState &s, cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (gfast)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slide_kernel<W, P, true>, kSlideThreads, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slide_kernel<W, P, false>, kSlideThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slide_kernel<W, P, LAY>, kSlideThreads, 0);
   if (per_sm < 1) per_sm = 1;
   const uint64_t want = ((d.Z >> 2) + kSlideThreads - 1) / kSlideThreads;
   uint64_t grid = (uint64_t)sms * per_sm;
@@ -222,21 +240,25 @@ cudaError_t launch_slide_t(const Dims &d, const DevState &s, bool gfast, cudaStr
   // k replicated into every even field (the subtrahend of the active test)
   uint32_t krep = 0;
   for (uint32_t f = 0; f < Fields<W>::F; f += 2) krep |= d.k << (f * W);
-  if (gfast)
-    slide_kernel<W, P, true><<<(unsigned)grid, kSlideThreads, 0, st>>>(d, s, krep);
-  else
-    slide_kernel<W, P, false><<<(unsigned)grid, kSlideThreads, 0, st>>>(d, s, krep);
+  slide_kernel<W, P, LAY><<<(unsigned)grid, kSlideThreads, 0, st>>>(d, s, krep);
   return cudaGetLastError();
+}
+
+template <int W, int P>
+cudaError_t launch_slide_t(const Dims &d, const DevState &s, int layout, cudaStream_t st) {
+  if (layout == kLayoutGfast) return launch_slide_l<W, P, kLayoutGfast>(d, s, st);
+  if (layout == kLayoutSerial) return launch_slide_l<W, P, kLayoutSerial>(d, s, st);
+  return launch_slide_l<W, P, kLayoutGsmall>(d, s, st);
 }
 
 // P = ceil(R / floor(32 / W)) DRV words per BDR, R = 32 - b_min in 16..31.
 template <int W>
-cudaError_t launch_slide_w(const Dims &d, const DevState &s, bool gfast, cudaStream_t st) {
+cudaError_t launch_slide_w(const Dims &d, const DevState &s, int layout, cudaStream_t st) {
   constexpr int F = 32 / W;
   constexpr int PLO = (16 + F - 1) / F, PHI = (31 + F - 1) / F;
   switch (d.P) {
 #define VBK_SLIDE_P(PP) \
-    case PP: if constexpr (PP >= PLO && PP <= PHI) return launch_slide_t<W, PP>(d, s, gfast, st); break;
+    case PP: if constexpr (PP >= PLO && PP <= PHI) return launch_slide_t<W, PP>(d, s, layout, st); break;
     VBK_SLIDE_P(1) VBK_SLIDE_P(2) VBK_SLIDE_P(3) VBK_SLIDE_P(4) VBK_SLIDE_P(5) VBK_SLIDE_P(6)
     VBK_SLIDE_P(7) VBK_SLIDE_P(8) VBK_SLIDE_P(9) VBK_SLIDE_P(10) VBK_SLIDE_P(11) VBK_SLIDE_P(12)
     VBK_SLIDE_P(13) VBK_SLIDE_P(14) VBK_SLIDE_P(15) VBK_SLIDE_P(16) VBK_SLIDE_P(31)
@@ -248,16 +270,16 @@ cudaError_t launch_slide_w(const Dims &d, const DevState &s, bool gfast, cudaStr
 
 }  // namespace
 
-cudaError_t launch_slide(const Dims &d, const DevState &s, bool gfast, cudaStream_t st) {
+cudaError_t launch_slide(const Dims &d, const DevState &s, int layout, cudaStream_t st) {
   switch (d.w) {
-    case 1: return launch_slide_w<1>(d, s, gfast, st);
-    case 2: return launch_slide_w<2>(d, s, gfast, st);
-    case 3: return launch_slide_w<3>(d, s, gfast, st);
-    case 4: return launch_slide_w<4>(d, s, gfast, st);
-    case 5: return launch_slide_w<5>(d, s, gfast, st);
-    case 6: return launch_slide_w<6>(d, s, gfast, st);
-    case 7: return launch_slide_w<7>(d, s, gfast, st);
-    case 8: return launch_slide_w<8>(d, s, gfast, st);
+    case 1: return launch_slide_w<1>(d, s, layout, st);
+    case 2: return launch_slide_w<2>(d, s, layout, st);
+    case 3: return launch_slide_w<3>(d, s, layout, st);
+    case 4: return launch_slide_w<4>(d, s, layout, st);
+    case 5: return launch_slide_w<5>(d, s, layout, st);
+    case 6: return launch_slide_w<6>(d, s, layout, st);
+    case 7: return launch_slide_w<7>(d, s, layout, st);
+    case 8: return launch_slide_w<8>(d, s, layout, st);
     default: return cudaErrorInvalidValue;
   }
 }

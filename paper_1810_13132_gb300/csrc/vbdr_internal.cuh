@@ -11,6 +11,7 @@
 //           contiguous 4*Z-byte plane, so the hot random updates of the
 //           gsmall scan touch a quarter of the DRV footprint.
 //   bs    : Z uint32, bsLBP1 of the gfast layout (bit r-1 <-> LBP1 r).
+//   now   : Zs uint8, nowLBP1 of the serial layout (the slice's largest LBP1).
 //   reg   : Z uint8, register of every BDR at the last slide (Alg. 2).
 //   ktab  : max(g_max, 512) KEnt, the premixed seed mix64(s1(i)) of virtual
 //           index i, s1(i) = H(i,2^32,A0) (the first hash of Alg. 3, which
@@ -28,6 +29,7 @@ struct vbdr_mlp;
 namespace vbk {
 
 constexpr int kMaxLog2G = 16;
+constexpr int kLayoutGfast = 0, kLayoutGsmall = 1, kLayoutSerial = 2;  // vbdr_layout
 constexpr int kKtabSize = 512;  // virtual indices covered by the smem table
 constexpr int kLnTab = 513;     // ln(v) tabulated for v = 0..512 (entry 0 unused)
 
@@ -111,6 +113,7 @@ struct EstConst {
 struct DevState {
   uint32_t *drv;     // [P][Zs]
   uint32_t *bs;      // [Z] (gfast only, else nullptr)
+  uint8_t *now;      // [Zs] nowLBP1 (serial only, else nullptr)
   uint8_t *reg;      // [Z]
   KEnt *ktab;        // [max(g_max, kKtabSize)]
   double *lnv;       // [kLnTab] ln(v)
@@ -125,10 +128,10 @@ __device__ __forceinline__ uint32_t host_b(const Dims &d, uint32_t aip) {
 
 // ----- launchers (defined in the kernel translation units) -----
 cudaError_t launch_init(const Dims &d, const DevState &s, cudaStream_t st);
-cudaError_t launch_scan(const Dims &d, const DevState &s, bool gfast,
+cudaError_t launch_scan(const Dims &d, const DevState &s, int layout,
                         const uint32_t *pairs, uint64_t n, cudaStream_t st,
                         const uint64_t *n_dev = nullptr);
-cudaError_t launch_slide(const Dims &d, const DevState &s, bool gfast,
+cudaError_t launch_slide(const Dims &d, const DevState &s, int layout,
                          cudaStream_t st);
 // Launch shape of the estimate kernel: lanes cooperating on one host and
 // threads per block.  kEstCandidates is the autotuner's search space; the

@@ -15,8 +15,8 @@ import numpy as np
 
 from . import _build
 
-VBDR_GFAST, VBDR_GSMALL = 0, 1
-LAYOUTS = {"gfast": VBDR_GFAST, "gsmall": VBDR_GSMALL}
+VBDR_GFAST, VBDR_GSMALL, VBDR_SERIAL = 0, 1, 2
+LAYOUTS = {"gfast": VBDR_GFAST, "gsmall": VBDR_GSMALL, "serial": VBDR_SERIAL}
 
 STATUS = {0: "VBDR_OK", -1: "VBDR_EINVAL", -2: "VBDR_ENOMEM", -3: "VBDR_ECUDA",
           -4: "VBDR_ERANGE", -5: "VBDR_EORDER", -6: "VBDR_ETIMEOUT"}

@@ -50,7 +50,7 @@ def _cfg(**kw):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(k=0), dict(k=256), dict(layout=2), dict(reserved=1), dict(group_rule=2),
+    dict(k=0), dict(k=256), dict(layout=3), dict(reserved=1), dict(group_rule=2),
     dict(log2_g=0), dict(log2_g=17), dict(num_bdr=0), dict(num_bdr=(1 << 32) + 1),
     dict(num_bdr=128),  # Z must exceed g = 128
     dict(group_rule=1, log2_g_min=7),  # b_min + 3 > 9

@@ -39,11 +39,16 @@ def _make(layout, k, Z, b, b_min=None, group_rule=0, seed=SEED):
     return v, o
 
 
+def _slice_max_state(os_, layout):
+    # the per-slice state of the layout: bsLBP1 (gfast), nowLBP1 (serial)
+    return os_["now"].astype(np.uint32) if layout == "serial" else os_["bs"]
+
+
 def _compare_state(v, o, tag=""):
     gs, os_ = v.state(), o.state()
     np.testing.assert_array_equal(gs["reg"], os_["reg"], err_msg=f"reg {tag}")
     np.testing.assert_array_equal(gs["dr"], os_["dr"], err_msg=f"dr {tag}")
-    np.testing.assert_array_equal(gs["bs"], os_["bs"], err_msg=f"bs {tag}")
+    np.testing.assert_array_equal(gs["bs"], _slice_max_state(os_, v.cfg.layout), err_msg=f"bs {tag}")
     assert v.pool_sums() == o.pool_sums(), tag
 
 
@@ -80,12 +85,12 @@ def _run(layout, k, Z, b, slices, aips, b_min=None, group_rule=0, every=True,
 def _compare_state_scan(v, o, tag):
     gs, os_ = v.state(), o.state()
     np.testing.assert_array_equal(gs["dr"], os_["dr"], err_msg=f"dr {tag}")
-    np.testing.assert_array_equal(gs["bs"], os_["bs"], err_msg=f"bs {tag}")
+    np.testing.assert_array_equal(gs["bs"], _slice_max_state(os_, v.cfg.layout), err_msg=f"bs {tag}")
 
 
 # ---------------------------------------------------------------- workloads
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
 def test_small_workload_every_slice(layout):
     """The small configuration at full size: k=10, 1e5 pairs per slice,
     1000 Zipf(1.1) hosts capped at 5000, Z = 2^16, g = 128; 13 slices so
@@ -96,7 +101,7 @@ def test_small_workload_every_slice(layout):
     _run(layout, cfg["k"], cfg["Z"], cfg["log2_g"], slices, gen.aips)
 
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
 def test_trace_shape_downscaled(layout):
     """Trace-shaped traffic (Zipf 1.05, 10% in-slice repeats, k=30, g=256)
     at 1/64 of the pairs and hosts, 1/64 of the pool; 33 slices."""
@@ -105,7 +110,7 @@ def test_trace_shape_downscaled(layout):
     _run(layout, 30, 1 << 18, 8, slices, gen.aips, every=False)
 
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
 def test_mixed_g_groups(layout):
     """Four host groups g = 64..512 in one pool (b_min = 6, R = 26, k = 60)."""
     rng = np.random.default_rng(103)
@@ -116,7 +121,7 @@ def test_mixed_g_groups(layout):
 
 # --------------------------------------------------------------- edge cases
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
 def test_empty_single_and_odd_slices(layout):
     rng = np.random.default_rng(104)
     aips = traffic.distinct_u32(rng, 50)
@@ -125,7 +130,7 @@ def test_empty_single_and_odd_slices(layout):
     _run(layout, 4, 4099, 5, slices, aips)
 
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
 @pytest.mark.parametrize("k", [1, 15])
 def test_discrete_window_and_k_at_dr_max(layout, k):
     """k = 1 (discrete window) and k = 15 = DR_MAX with w = 4."""
@@ -136,7 +141,7 @@ def test_discrete_window_and_k_at_dr_max(layout, k):
     _run(layout, k, 10007, 7, slices, aips)
 
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
 def test_max_contention_one_host(layout):
     """Every pair to one aip with g = 2: all updates hit two BDRs."""
     rng = np.random.default_rng(106)
@@ -145,7 +150,7 @@ def test_max_contention_one_host(layout):
     _run(layout, 3, 1000, 1, slices, aip)
 
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
 def test_duplicate_heavy_and_split_scans(layout):
     """Bursts of identical pairs inside a warp, and one slice scanned in
     several calls: same state as the single-call oracle."""
@@ -159,7 +164,7 @@ def test_duplicate_heavy_and_split_scans(layout):
     _run(layout, 5, 8191, 6, slices, aips, split=7)
 
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
 def test_order_independence_on_gpu(layout):
     from paper_1810_13132_gb300 import Config, Vbdr
     rng = np.random.default_rng(108)
@@ -176,25 +181,31 @@ def test_order_independence_on_gpu(layout):
         np.testing.assert_array_equal(sa[key], sb[key])
 
 
-def test_gsmall_and_gfast_registers_agree_on_gpu():
-    """Sec. 4.2: both GPU variants yield the same registers (and estimates)."""
+def test_all_layouts_agree_on_gpu():
+    """Sec. 4.2: the GPU variants yield the same registers (and estimates);
+    serial and gfast also hold the same DRV (Alg. 1 and Alg. 6 fold the same
+    slice maximum)."""
     from paper_1810_13132_gb300 import Config, Vbdr
     gen = traffic.ZipfTraffic(2000, 1.1, 5000, 6, seed=109)
     a = Vbdr(Config(k=6, num_bdr=1 << 16, log2_g=7, layout="gfast"))
     b = Vbdr(Config(k=6, num_bdr=1 << 16, log2_g=7, layout="gsmall"))
+    c = Vbdr(Config(k=6, num_bdr=1 << 16, log2_g=7, layout="serial"))
     for _ in range(9):
         s = _dev(gen.next_slice(100_000))
-        for v in (a, b):
+        for v in (a, b, c):
             v.scan(s)
             v.slide()
         np.testing.assert_array_equal(a.registers(), b.registers())
+        np.testing.assert_array_equal(a.registers(), c.registers())
+        np.testing.assert_array_equal(a.state()["dr"], c.state()["dr"])
     aips = _dev(gen.aips)
     assert torch.equal(a.estimate(aips), b.estimate(aips))
+    assert torch.equal(a.estimate(aips), c.estimate(aips))
 
 
 # --------------------------------------------------------- host-buffer path
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
 def test_host_buffer_entry_points(layout):
     """vbdr_scan_slice_host / vbdr_estimate_host (pinned and pageable) give
     the same state and estimates as the device-buffer calls."""
@@ -240,7 +251,7 @@ def test_misaligned_pairs_rejected():
 
 # ------------------------------------------------ full-size trace, sampled
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
 def test_trace_full_size_two_slices(layout):
     """The trace configuration at full size (N = 64M pairs per slice, 1M
     hosts, Z = 2^24, g = 256, k = 30, 10% repeats), two slices in the launch
