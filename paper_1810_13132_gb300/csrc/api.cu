@@ -463,6 +463,96 @@ int vbdr_autotune_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts, f
   return VBDR_OK;
 }
 
+namespace {
+// Checkpoint layout: header, then the raw device buffers in a fixed order.
+struct CkptHeader {
+  char magic[8];  // "VBDRCKP1"
+  uint32_t k, log2_g, log2_g_min, group_rule, layout, slid;
+  uint64_t num_bdr, seed, drv_bytes, slice_bytes, reg_bytes;
+};
+
+void ckpt_sizes(const vbdr *h, uint64_t *drv, uint64_t *slice, uint64_t *reg) {
+  *drv = (uint64_t)h->d.P * h->d.Zs * 4;
+  *slice = h->s.bs ? h->d.Z * 4 : (h->s.now ? h->d.Zs : 0);
+  *reg = h->d.Zs;
+}
+
+void fill_header(const vbdr *h, CkptHeader *hd) {
+  std::memset(hd, 0, sizeof(*hd));
+  std::memcpy(hd->magic, "VBDRCKP1", 8);
+  hd->k = h->d.k;
+  hd->log2_g = h->d.b;
+  hd->log2_g_min = h->d.b_min;
+  hd->group_rule = h->d.group_rule;
+  hd->layout = (uint32_t)h->layout;
+  hd->slid = h->slid ? 1u : 0u;
+  hd->num_bdr = h->d.Z;
+  hd->seed = h->d.A0;
+  ckpt_sizes(h, &hd->drv_bytes, &hd->slice_bytes, &hd->reg_bytes);
+}
+}  // namespace
+
+int vbdr_state_bytes(vbdr_t h, uint64_t *bytes) {
+  if (!h || !bytes) return VBDR_EINVAL;
+  uint64_t a, b, c;
+  ckpt_sizes(h, &a, &b, &c);
+  *bytes = sizeof(CkptHeader) + a + b + c + 2 * sizeof(unsigned long long);
+  return VBDR_OK;
+}
+
+int vbdr_save(vbdr_t h, void *h_buf, uint64_t cap, void *stream) {
+  if (!h || !h_buf) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  uint64_t need = 0;
+  vbdr_state_bytes(h, &need);
+  if (cap < need) return VBDR_ERANGE;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fail_cuda(h, e);
+  CkptHeader hd;
+  fill_header(h, &hd);
+  uint8_t *p = static_cast<uint8_t *>(h_buf);
+  std::memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  e = cudaMemcpy(p, h->s.drv, hd.drv_bytes, cudaMemcpyDeviceToHost);
+  p += hd.drv_bytes;
+  if (e == cudaSuccess && hd.slice_bytes)
+    e = cudaMemcpy(p, h->s.bs ? (void *)h->s.bs : (void *)h->s.now, hd.slice_bytes,
+                   cudaMemcpyDeviceToHost);
+  p += hd.slice_bytes;
+  if (e == cudaSuccess) e = cudaMemcpy(p, h->s.reg, hd.reg_bytes, cudaMemcpyDeviceToHost);
+  p += hd.reg_bytes;
+  if (e == cudaSuccess) e = cudaMemcpy(p, h->s.sums, 2 * sizeof(unsigned long long),
+                                       cudaMemcpyDeviceToHost);
+  return fail_cuda(h, e);
+}
+
+int vbdr_load(vbdr_t h, const void *h_buf, uint64_t len, void *stream) {
+  if (!h || !h_buf) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  uint64_t need = 0;
+  vbdr_state_bytes(h, &need);
+  if (len < need) return VBDR_EINVAL;
+  CkptHeader mine, hd;
+  fill_header(h, &mine);
+  std::memcpy(&hd, h_buf, sizeof(hd));
+  mine.slid = hd.slid;  // the one field that may differ
+  if (std::memcmp(&mine, &hd, sizeof(hd)) != 0) return VBDR_EINVAL;  // other configuration
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  const uint8_t *p = static_cast<const uint8_t *>(h_buf) + sizeof(hd);
+  if (e == cudaSuccess) e = cudaMemcpy(h->s.drv, p, hd.drv_bytes, cudaMemcpyHostToDevice);
+  p += hd.drv_bytes;
+  if (e == cudaSuccess && hd.slice_bytes)
+    e = cudaMemcpy(h->s.bs ? (void *)h->s.bs : (void *)h->s.now, p, hd.slice_bytes,
+                   cudaMemcpyHostToDevice);
+  p += hd.slice_bytes;
+  if (e == cudaSuccess) e = cudaMemcpy(h->s.reg, p, hd.reg_bytes, cudaMemcpyHostToDevice);
+  p += hd.reg_bytes;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->s.sums, p, 2 * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) h->slid = hd.slid != 0;
+  return fail_cuda(h, e);
+}
+
 int vbdr_copy_state(vbdr_t h, uint8_t *h_dr, uint32_t *h_bs, uint8_t *h_reg,
                     void *stream) {
   if (!h) return VBDR_EINVAL;

@@ -79,6 +79,9 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "vbdr_server_in_use": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U32)]),
+    "vbdr_state_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(_U64)]),
+    "vbdr_save": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
+    "vbdr_load": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
     "vbdr_estimate_registers_noalloc": (ctypes.c_int, [_VP, _U64, _U32, _U64, _VP, _U64, _VP,
                                                        _VP]),
 }
@@ -255,6 +258,18 @@ class Vbdr:
         _check("vbdr_estimate_learned", self._L.vbdr_estimate_learned(
             self._h, mlp._h, aips.data_ptr(), n, out.data_ptr(), _stream_ptr(stream)))
         return out
+
+    # -- checkpoint / resume -------------------------------------------------------
+    def save(self, stream=None) -> bytes:
+        n = ctypes.c_uint64()
+        _check("vbdr_state_bytes", self._L.vbdr_state_bytes(self._h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check("vbdr_save", self._L.vbdr_save(self._h, buf, n.value, _stream_ptr(stream)))
+        return buf.raw
+
+    def load(self, blob: bytes, stream=None) -> None:
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check("vbdr_load", self._L.vbdr_load(self._h, buf, len(blob), _stream_ptr(stream)))
 
     # -- inspection --------------------------------------------------------------
     def state(self, stream=None) -> dict:
