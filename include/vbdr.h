@@ -261,7 +261,8 @@ VBDR_API int vbdr_mlp_train(vbdr_mlp_t m, const uint16_t *d_X, const float *d_y,
 VBDR_API int vbdr_mlp_gradient(vbdr_mlp_t m, const uint16_t *d_X, const float *d_y, uint64_t n,
                                float *h_grad, float *h_loss, void *stream);
 
-/* delta for n feature rows (d_X BF16 [n][48], d_delta FP32 [n], device). */
+/* delta for n feature rows (d_X BF16 [n][48], 16-byte aligned; d_delta FP32
+ * [n]; both device).  Errors: VBDR_EINVAL (NULL or misaligned), VBDR_ECUDA. */
 VBDR_API int vbdr_mlp_forward(vbdr_mlp_t m, const uint16_t *d_X, uint64_t n, float *d_delta,
                               void *stream);
 

@@ -335,19 +335,27 @@ __global__ void refresh_bf16_kernel(const float *theta, __nv_bfloat16 *w1c, __nv
   }
 }
 
-// One warp per 32 rows: copy the rows' features into a padded shared tile
-// (16-byte chunks), run the network; optional correction of est in place.
-__device__ __forceinline__ void stage_rows(const __nv_bfloat16 *X, uint64_t n, uint64_t r0,
-                                           __nv_bfloat16 *xs) {
+// 16-byte asynchronous copy global -> shared (zero-filled when src_bytes = 0).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Start copying rows [r0, r0 + 32) of X into a padded tile (rows past n: 0).
+__device__ __forceinline__ void prefetch_rows(const __nv_bfloat16 *X, uint64_t n, uint64_t r0,
+                                              __nv_bfloat16 *xs) {
   const int lane = threadIdx.x & 31;
-  const uint64_t rows = n - r0 < 32 ? n - r0 : 32;
-  const uint4 *src = reinterpret_cast<const uint4 *>(X + r0 * kMlpLive);
   for (int i = lane; i < 32 * (kMlpLive / 8); i += 32) {
     const int r = i / (kMlpLive / 8), q = i % (kMlpLive / 8);
-    *reinterpret_cast<uint4 *>(xs + r * kXLd + 8 * q) =
-        (uint64_t)r < rows ? src[i] : make_uint4(0, 0, 0, 0);
+    const bool ok = r0 + r < n;
+    cp_async16(xs + r * kXLd + 8 * q, ok ? (const void *)(X + (r0 + r) * kMlpLive + 8 * q)
+                                          : (const void *)X, ok ? 16u : 0u);
   }
-  __syncwarp();
+  cp_async_commit();
 }
 
 template <int WARPS>
@@ -365,58 +373,73 @@ __device__ __forceinline__ MlpDevWeights stage_weights(const MlpDevWeights &w, u
   return MlpDevWeights{w1s, w2s, bs, bs + kMlpHid, bs + 2 * kMlpHid, bs + 3 * kMlpHid};
 }
 
-constexpr int kFwdWarps = 4;  // 46 KB of static shared memory per block
+constexpr int kFwdWarps = 8;
 
-__global__ void __launch_bounds__(kFwdWarps * 32)
-    forward_kernel(const __nv_bfloat16 *__restrict__ X, uint64_t n, MlpDevWeights w,
-                   float *__restrict__ delta) {
-  __shared__ uint2 w1s[kW1Frags], w2s[kW2Frags];
-  __shared__ float bs[3 * kMlpHid + 1];
-  __shared__ __align__(16) __nv_bfloat16 xs[kFwdWarps][32 * kXLd];
-  __shared__ __align__(16) __nv_bfloat16 h1s[kFwdWarps][32 * kHLd];
-  const MlpDevWeights ws = stage_weights<kFwdWarps>(w, w1s, w2s, bs);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t warps = (uint64_t)gridDim.x * kFwdWarps;
-  for (uint64_t r0 = ((uint64_t)blockIdx.x * kFwdWarps + warp) * 32; r0 < n; r0 += warps * 32) {
-    stage_rows(X, n, r0, xs[warp]);
-    const float d = mlp_forward_warp(xs[warp], h1s[warp], ws);
-    if (r0 + lane < n) delta[r0 + lane] = d;
-  }
-}
+// Shared memory of the forward / correction kernels (dynamic, > 48 KB).
+struct FwdSmem {
+  uint2 w1s[kW1Frags];
+  uint2 w2s[kW2Frags];
+  float bs[3 * kMlpHid + 4];
+  __nv_bfloat16 xs[kFwdWarps][2][32 * kXLd];  // double-buffered input rows
+  __nv_bfloat16 h1s[kFwdWarps][16 * kHLd];     // one tile's hidden layer
+};
 
-// Learned correction of plain estimates from feature rows: weights staged in
-// shared memory once per block, then 32 hosts per warp on the tensor cores;
-// est[i] (the plain estimate) is replaced by the corrected one unless it
-// exceeds nmax.
+// One warp per 32 rows (grid-stride); the next task's rows are copied in
+// while the current ones run through the network.  CORRECT: est (the plain
+// estimates) is replaced by the corrected estimate unless above nmax;
+// otherwise delta is written to est.
+template <bool CORRECT>
 __global__ void __launch_bounds__(kFwdWarps * 32)
-    correct_kernel(const __nv_bfloat16 *__restrict__ X, uint64_t n, MlpDevWeights w, float nmax,
-                   float *__restrict__ est) {
-  __shared__ uint2 w1s[kW1Frags], w2s[kW2Frags];
-  __shared__ float bs[3 * kMlpHid + 1];
-  __shared__ __align__(16) __nv_bfloat16 xs[kFwdWarps][32 * kXLd];
-  __shared__ __align__(16) __nv_bfloat16 h1s[kFwdWarps][32 * kHLd];
-  const MlpDevWeights ws = stage_weights<kFwdWarps>(w, w1s, w2s, bs);
+    mlp_rows_kernel(const __nv_bfloat16 *__restrict__ X, uint64_t n, MlpDevWeights w, float nmax,
+                    float *__restrict__ est) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FwdSmem &S = *reinterpret_cast<FwdSmem *>(smem_raw);
+  const MlpDevWeights ws = stage_weights<kFwdWarps>(w, S.w1s, S.w2s, S.bs);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t warps = (uint64_t)gridDim.x * kFwdWarps;
-  for (uint64_t r0 = ((uint64_t)blockIdx.x * kFwdWarps + warp) * 32; r0 < n; r0 += warps * 32) {
-    stage_rows(X, n, r0, xs[warp]);
-    const float d = mlp_forward_warp(xs[warp], h1s[warp], ws);
-    if (r0 + lane < n) {
-      const float plain = est[r0 + lane];
-      float corr = expm1f(log1pf(plain) + d);
-      if (!(corr > 0.f)) corr = 0.f;
-      est[r0 + lane] = plain > nmax ? plain : corr;
+  const uint64_t step = (uint64_t)gridDim.x * kFwdWarps * 32;
+  uint64_t r0 = ((uint64_t)blockIdx.x * kFwdWarps + warp) * 32;
+  int buf = 0;
+  if (r0 < n) prefetch_rows(X, n, r0, S.xs[warp][0]);
+  for (; r0 < n; r0 += step, buf ^= 1) {
+    if (r0 + step < n) {
+      prefetch_rows(X, n, r0 + step, S.xs[warp][buf ^ 1]);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
+    __syncwarp();
+    const float d = mlp_forward_warp(S.xs[warp][buf], S.h1s[warp], ws);
+    if (r0 + lane < n) {
+      if constexpr (CORRECT) {
+        const float plain = est[r0 + lane];
+        float corr = expm1f(log1pf(plain) + d);
+        if (!(corr > 0.f)) corr = 0.f;
+        est[r0 + lane] = plain > nmax ? plain : corr;
+      } else {
+        est[r0 + lane] = d;
+      }
+    }
+    __syncwarp();  // the buffer is refilled two tasks later
   }
 }
 
-int grid_of(uint64_t units, int threads) {
-  int dev = 0, sms = 0;
+template <bool CORRECT>
+cudaError_t launch_mlp_rows(const __nv_bfloat16 *X, uint64_t n, MlpDevWeights w, float nmax,
+                            float *est, cudaStream_t st) {
+  const int smem = (int)sizeof(FwdSmem);
+  cudaError_t e = cudaFuncSetAttribute(mlp_rows_kernel<CORRECT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint64_t g = (units + threads - 1) / threads;
-  if (g > (uint64_t)sms * 16) g = (uint64_t)sms * 16;
-  return g ? (int)g : 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_rows_kernel<CORRECT>, kFwdWarps * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t tasks = (n + 31) / 32;
+  uint64_t grid = (tasks + kFwdWarps - 1) / kFwdWarps;
+  if (grid > (uint64_t)sms * per_sm) grid = (uint64_t)sms * per_sm;  // persistent wave
+  mlp_rows_kernel<CORRECT><<<(unsigned)grid, kFwdWarps * 32, smem, st>>>(X, n, w, nmax, est);
+  return cudaGetLastError();
 }
 
 // splitmix64 stream for the initial weights (uniform(-a, a) per layer)
@@ -608,11 +631,9 @@ int vbdr_mlp_forward(vbdr_mlp_t m, const uint16_t *d_X, uint64_t n, float *d_del
   if (!m) return VBDR_EINVAL;
   if (m->sticky) return m->sticky;
   if (n == 0) return VBDR_OK;
-  if (!d_X || !d_delta) return VBDR_EINVAL;
-  MlpDevWeights w = mlp_weights(m);
-  forward_kernel<<<grid_of((n + 31) / 32, kFwdWarps), kFwdWarps * 32, 0, (cudaStream_t)stream>>>(
-      reinterpret_cast<const __nv_bfloat16 *>(d_X), n, w, d_delta);
-  return mlp_fail(m, cudaGetLastError());
+  if (!d_X || !d_delta || ((uintptr_t)d_X & 15)) return VBDR_EINVAL;
+  return mlp_fail(m, launch_mlp_rows<false>(reinterpret_cast<const __nv_bfloat16 *>(d_X), n,
+                                            mlp_weights(m), 0.f, d_delta, (cudaStream_t)stream));
 }
 
 }  // extern "C"
@@ -621,9 +642,7 @@ namespace vbk {
 cudaError_t launch_mlp_correct(const vbdr_mlp *m, const __nv_bfloat16 *X, uint64_t n, float *est,
                                cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  correct_kernel<<<grid_of((n + 31) / 32, kFwdWarps), kFwdWarps * 32, 0, st>>>(X, n, mlp_weights(m),
-                                                                              m->nmax, est);
-  return cudaGetLastError();
+  return launch_mlp_rows<true>(X, n, mlp_weights(m), m->nmax, est, st);
 }
 
 MlpDevWeights mlp_weights(const vbdr_mlp *m) {

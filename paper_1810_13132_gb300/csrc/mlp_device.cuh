@@ -139,7 +139,8 @@ __device__ __forceinline__ void load_a_tile(uint32_t (&a)[4], const __nv_bfloat1
 // Forward of 32 rows by one warp, one 16-row tile at a time (32 FP32
 // accumulators live instead of 64, for occupancy).  xs: the rows' live
 // inputs, BF16 [32][kXLd] (first kMlpLive columns used); h1s: scratch BF16
-// [32][kHLd].  Returns delta of row (lane) in every lane.
+// [16][kHLd] (one tile's hidden layer).  Returns delta of row (lane) in every
+// lane.
 __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
                                                   __nv_bfloat16 *h1s,
                                                   const MlpDevWeights &w) {
@@ -169,7 +170,7 @@ __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
     for (int n = 0; n < 8; ++n)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int r = 16 * m + g + 8 * h, j = 8 * n + c;
+        const int r = g + 8 * h, j = 8 * n + c;
         const __nv_bfloat162 z = __floats2bfloat162_rn(acc[n][2 * h] + w.b1[j],
                                                        acc[n][2 * h + 1] + w.b1[j + 1]);
         *reinterpret_cast<__nv_bfloat162 *>(h1s + r * kHLd + j) = gelu_bf16x2(z);
@@ -183,7 +184,7 @@ __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
 #pragma unroll
     for (int kk = 0; kk < kMlpHid / 16; ++kk) {
       uint32_t a[4];
-      load_a_tile(a, h1s + 16 * m * kHLd + 16 * kk, kHLd);
+      load_a_tile(a, h1s + 16 * kk, kHLd);
 #pragma unroll
       for (int n = 0; n < 8; ++n) {
         const uint2 f = w.w2f[(kk * 8 + n) * 32 + lane];
@@ -191,6 +192,7 @@ __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
         mma_bf16(acc[n], a, b);
       }
     }
+    __syncwarp();  // h1s is rewritten by the next tile
     // output layer in FP32: delta_r = sum_j GELU(z2[r][j]) w3[j] + b3
     part[m][0] = part[m][1] = 0.f;
 #pragma unroll
