@@ -42,6 +42,9 @@ def _args():
     p.add_argument("--workload", default="trace", choices=["trace", "small", "batched", "serve"])
     p.add_argument("--tenants", type=int, default=2, help="serve: concurrent tenants")
     p.add_argument("--slices-per-tenant", type=int, default=40, help="serve: timed slices")
+    p.add_argument("--estimate", default="planned", choices=["planned", "gather"],
+                   help="trace/small: estimate through a host-list plan (built once, outside "
+                        "the timed steps) or by gathering every virtual register")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mre", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -202,6 +205,21 @@ def run_ours(a):
     d_out = torch.empty(H, dtype=torch.float32, device="cuda")
     v = Vbdr(Config(k=wl["k"], num_bdr=wl["Z"], log2_g=wl["log2_g"], layout=a.layout, seed=SEED))
     stream = torch.cuda.current_stream()
+    planned = a.estimate == "planned"
+    plan = plan_info = None
+    if planned:
+        # the host list is fixed for the whole run: its plan is built once
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        plan = v.plan(d_aips)
+        torch.cuda.synchronize()
+        plan_info = dict(plan.info(), build_ms=round((time.perf_counter() - w0) * 1e3, 2))
+
+    def estimate_step():
+        if planned:
+            v.estimate_planned(plan, out=d_out)
+        else:
+            v.estimate(d_aips, out=d_out)
 
     def step(i, ev=None):
         if ev is not None:
@@ -212,7 +230,7 @@ def run_ours(a):
         v.slide()
         if ev is not None:
             ev[2].record(stream)
-        v.estimate(d_aips, out=d_out)
+        estimate_step()
         if ev is not None:
             ev[3].record(stream)
 
@@ -239,6 +257,24 @@ def run_ours(a):
     est_ms = [e[2].elapsed_time(e[3]) for e in evs]
     ms_step = total_ms / a.steps
     value = (N * ws * a.steps) / (total_ms * 1e-3) / 1e9
+
+    # the gather estimate on the same state, for comparison; the planned
+    # result must equal it bit for bit
+    gather = None
+    if planned:
+        d_ref = torch.empty(H, dtype=torch.float32, device="cuda")
+        v.estimate(d_aips, out=d_ref)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(d_ref.view(torch.int32), d_out.view(torch.int32)))
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(a.steps):
+            v.estimate(d_aips, out=d_ref)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        plan.status()
+        gather = {"estimate_gather_ms": round(g0.elapsed_time(g1) / a.steps, 4),
+                  "planned_equals_gather": same}
 
     # learned correction (weights trained by tests/train_correction.py): the
     # fused estimate + MLP kernel timed on the same state as the plain one
@@ -290,7 +326,10 @@ def run_ours(a):
         def e2e_step(i):
             v2.scan_host(pinned[i % nsl])
             v2.slide()
-            v2.estimate_host(h_aips, h_out)
+            if planned:  # the plan serves every handle of this configuration
+                v2.estimate_planned_host(plan, h_out)
+            else:
+                v2.estimate_host(h_aips, h_out)
             torch.cuda.current_stream().synchronize()  # result read back on the host
 
         for i in range(a.warmup):
@@ -307,7 +346,7 @@ def run_ours(a):
         torch.cuda.synchronize()
         e2e_ms = _barrier_max(dist, e0.elapsed_time(e1))
         e2e = {"value": round((N * ws * a.steps) / (e2e_ms * 1e-3) / 1e9, 3),
-               "unit": "G pairs/s", "h2d_bytes_per_step": 8 * N + 4 * H,
+               "unit": "G pairs/s", "h2d_bytes_per_step": 8 * N + (0 if planned else 4 * H),
                "d2h_bytes_per_step": 4 * H, "ms_per_step": round(e2e_ms / a.steps, 3)}
         v2.close()
 
@@ -318,21 +357,26 @@ def run_ours(a):
                    "gsmall": Z * (4 * P + 4 * P + 1),               # DRV in, DRV + reg out
                    "serial": Z * ((4 * P + 1) + (4 * P + 1 + 1))}[a.layout]  # DRV + nowLBP1
     est_bytes = H * (4 + 4) + Z
+    if planned:  # the plan is read once per launch: host list, group offsets, entries
+        est_bytes = plan_info["device_bytes"] + 4 * H + Z
     kern = {"scan": (statistics.mean(scan_ms), scan_bytes),
             "slide": (statistics.mean(slide_ms), slide_bytes),
             "estimate": (statistics.mean(est_ms), est_bytes)}
     dom = max(kern, key=lambda k: kern[k][0])
     dms, dbytes = kern[dom]
     achieved = dbytes / (dms * 1e-3) / 1e9
-    traffic_bytes = _ncu_traffic(dom, a.layout, a.workload)
+    tkey = {"estimate": "estimate_planned" if planned else "estimate"}
+    traffic_bytes = _ncu_traffic(tkey.get(dom, dom), a.layout, a.workload)
     per_kernel = {}
     for name, (ms, nbytes) in kern.items():
         gbs = nbytes / (ms * 1e-3) / 1e9
         per_kernel[name] = {"ms": round(ms, 4), "algorithmic_bytes": int(nbytes),
                             "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
-                            "traffic": _ncu_traffic(name, a.layout, a.workload)}
-    limiter = {"estimate": "L1TEX/L2 rate of random 1-byte register gathers (ncu: L1TEX 96%, L2 73%, "
-                           "99% L2 hits); DRAM carries only hosts and the 16 MiB register array",
+                            "traffic": _ncu_traffic(tkey.get(name, name), a.layout, a.workload)}
+    limiter = {"estimate": ("shared-memory pipe: one random byte read and one shared atomic per "
+                            "plan entry; DRAM carries the plan stream" if planned else
+                            "L1TEX/L2 rate of random 1-byte register gathers (ncu: L1TEX 96%, L2 73%, "
+                            "99% L2 hits); DRAM carries only hosts and the 16 MiB register array"),
                "scan": "L2 random-sector rate of the update-word test loads plus the hash arithmetic",
                "slide": "HBM streaming of the DRV planes with the SWAR field arithmetic"}[dom]
     cpu = None
@@ -350,6 +394,8 @@ def run_ours(a):
                    "k": wl["k"], "pairs_per_slice": N, "hosts": H, "Z": Z,
                    "g": 1 << wl["log2_g"], "repeat_frac": wl["repeat_frac"],
                    "l2": "inputs larger than L2 (512 MiB per slice, 4 distinct slices cycled)",
+                   "estimate": ("planned: host-to-register plan of the fixed host list built once "
+                                "before the timed steps" if planned else "gather"),
                    "parallelism": f"replicas x{ws}"},
         "scan_gpairs_per_s": round(N / (statistics.mean(scan_ms) * 1e-3) / 1e9, 3),
         "scan_ms": round(statistics.mean(scan_ms), 4),
@@ -361,6 +407,8 @@ def run_ours(a):
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic_bytes, "peak_kind": peak_kind, "limiter": limiter},
         "kernels": per_kernel,
+        "plan": plan_info,
+        "gather_estimate": gather,
         "accuracy": mre,
         "learned_correction": learned,
         "e2e": e2e,

@@ -155,6 +155,51 @@ VBDR_API int vbdr_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts,
 VBDR_API int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n_hosts,
                        float *h_out, void *stream);
 
+/* Estimate plans.  The host-to-register map of Alg. 3 (host aip, virtual
+ * index i -> physical BDR) depends only on the host address, i and the
+ * handle's configuration, so a host list that is estimated after every slide
+ * can have it computed once.  A plan holds it grouped by 32 KiB register
+ * chunk; vbdr_estimate_planned then streams the register array through
+ * shared memory once per block of hosts instead of gathering H g random
+ * bytes.  The estimates equal vbdr_estimate's for the same hosts, bit for
+ * bit (same exact integer sums, same FP64 formula).
+ * Plans are valid for every handle with the same Z, log2_g, log2_g_min,
+ * group_rule and seed on the same device; they do not depend on the state.
+ * Memory: 4 bytes per virtual register of the list (H g in all, plus at most
+ * 3 per register chunk and block of hosts of padding), 4 bytes per host and
+ * 8 bytes per (block, chunk) pair. */
+typedef struct vbdr_plan *vbdr_plan_t;
+
+/* Build the plan of n_hosts hosts (d_aips: uint32 host addresses, device,
+ * 4-byte aligned; copied, so the buffer may be reused after the call).
+ * Synchronises the stream (the group sizes are read back to lay out the
+ * plan).  n_hosts = 0 gives an empty plan.
+ * Errors: VBDR_EINVAL (NULL or misaligned), VBDR_ERANGE (Z > 2^28),
+ * VBDR_ENOMEM, VBDR_ECUDA. */
+VBDR_API int vbdr_plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts,
+                              vbdr_plan_t *out, void *stream);
+/* Free a plan (NULL is accepted).  No call that uses it may be in flight. */
+VBDR_API int vbdr_plan_destroy(vbdr_plan_t p);
+/* Hosts, stored entries (including padding) and device bytes of a plan;
+ * any output pointer may be NULL.  Errors: VBDR_EINVAL. */
+VBDR_API int vbdr_plan_info(vbdr_plan_t p, uint64_t *n_hosts, uint64_t *n_entries,
+                            uint64_t *device_bytes);
+/* Synchronous check of the plan's device error word: VBDR_ETIMEOUT if a
+ * bounded wait inside an earlier vbdr_estimate_planned expired (that call's
+ * outputs for the affected block of hosts are NaN), else VBDR_OK. */
+VBDR_API int vbdr_plan_status(vbdr_plan_t p);
+
+/* vbdr_estimate for the plan's hosts, in the order given at vbdr_plan_create:
+ * d_out[i] (device, n_hosts floats, 4-byte aligned) is host i's estimate.
+ * Errors: VBDR_EINVAL (NULL, misaligned, plan built for another
+ * configuration or device), VBDR_EORDER (no slide yet), VBDR_ECUDA. */
+VBDR_API int vbdr_estimate_planned(vbdr_t h, vbdr_plan_t p, float *d_out, void *stream);
+
+/* vbdr_estimate_planned with the estimates written to HOST memory h_out
+ * (valid once the stream has passed the call), through a device buffer owned
+ * by the handle.  Errors: as vbdr_estimate_planned, plus VBDR_ENOMEM. */
+VBDR_API int vbdr_estimate_planned_host(vbdr_t h, vbdr_plan_t p, float *h_out, void *stream);
+
 /* Estimates for n_hosts hosts computed straight from a register array that
  * the caller already holds in device memory, without allocating anything.
  * The paper has no counterpart of this call; it serves callers that cannot

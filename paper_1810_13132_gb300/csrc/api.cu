@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of include/vbdr.h: argument checks, device state
 // ownership, host-buffer staging, and the state-initialisation kernel.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -33,6 +34,19 @@ struct vbdr {
   uint64_t est_cap;
   uint16_t *d_feat;     // feature rows of the learned estimate [feat_cap][48]
   uint64_t feat_cap;
+};
+
+// A host list's estimate plan (plan.cu): device arrays plus the handle
+// configuration it was built for.
+struct vbdr_plan {
+  int device;
+  uint64_t Z;
+  uint32_t b, b_min, group_rule;
+  uint64_t A0;
+  vbk::PlanDev dev;
+  uint32_t *aips;  // owned copy of the host list
+  uint64_t n_entries;
+  uint64_t bytes;  // device bytes held
 };
 
 namespace {
@@ -180,7 +194,12 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
     e = cudaMalloc(&h->s.now, (size_t)d.Zs);
     if (e == cudaSuccess) e = cudaMemset(h->s.now, 0, (size_t)d.Zs);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&h->s.reg, (size_t)d.Zs);  // whole 32-bit words
+  // registers: whole 32-bit words, and whole plan chunks (the planned
+  // estimate copies reg chunk by chunk)
+  const uint64_t reg_bytes =
+      std::max<uint64_t>(d.Zs, (d.Z + vbk::kPlanChunk - 1) / vbk::kPlanChunk * vbk::kPlanChunk);
+  if (e == cudaSuccess) e = cudaMalloc(&h->s.reg, (size_t)reg_bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->s.reg, 0, (size_t)reg_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->s.ktab, (size_t)kn * sizeof(vbk::KEnt));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.lnv, vbk::kLnTab * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.sums, 8 * sizeof(unsigned long long));
@@ -607,6 +626,171 @@ int vbdr_copy_pool_sums(vbdr_t h, uint64_t *S_Z, uint64_t *V_Z, void *stream) {
   *S_Z = v[0];
   *V_Z = v[1];
   return VBDR_OK;
+}
+
+/* ---------------------------------------------------------------- plans */
+
+int vbdr_plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n, vbdr_plan_t *out,
+                     void *stream) {
+  if (!h || !out) return VBDR_EINVAL;
+  *out = nullptr;
+  if (h->sticky) return h->sticky;
+  if (n > 0 && (!d_aips || ((uintptr_t)d_aips & 3u))) return VBDR_EINVAL;
+  const Dims &d = h->d;
+  const uint64_t nchunks = (d.Z + vbk::kPlanChunk - 1) / vbk::kPlanChunk;
+  if (nchunks > vbk::kPlanMaxChunks) return VBDR_ERANGE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (sms < 1) sms = 1;
+  // blocks of at most kPlanMaxHB hosts, a whole number of waves of one block per SM
+  const uint64_t per_wave = (uint64_t)sms * vbk::kPlanMaxHB;
+  const uint64_t waves = n ? (n + per_wave - 1) / per_wave : 0;
+  const uint64_t HB = n ? (n + (uint64_t)sms * waves - 1) / ((uint64_t)sms * waves) : 1;
+  const uint64_t NB = (n + HB - 1) / HB;
+
+  vbdr_plan *p = new (std::nothrow) vbdr_plan;
+  if (!p) return VBDR_ENOMEM;
+  std::memset(p, 0, sizeof(*p));
+  p->device = h->device;
+  p->Z = d.Z;
+  p->b = d.b;
+  p->b_min = d.b_min;
+  p->group_rule = d.group_rule;
+  p->A0 = d.A0;
+  vbk::PlanDev &pd = p->dev;
+  pd.n = n;
+  pd.HB = (uint32_t)HB;
+  pd.NB = (uint32_t)NB;
+  pd.nchunks = (uint32_t)nchunks;
+  const uint64_t ngroups = NB * nchunks;
+  std::vector<uint32_t> counts(ngroups);
+  std::vector<unsigned long long> goff(ngroups + 1);
+  cudaError_t e = cudaSuccess;
+  auto fail = [&](cudaError_t err) {
+    cudaGetLastError();
+    cudaFree(p->aips);
+    cudaFree(pd.entries);
+    cudaFree(pd.goff);
+    cudaFree(pd.counts);
+    cudaFree(pd.err);
+    delete p;
+    return err == cudaErrorMemoryAllocation ? VBDR_ENOMEM : fail_cuda(h, err);
+  };
+  e = cudaMalloc(&p->aips, std::max<uint64_t>(n, 1) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&pd.goff, (ngroups + 1) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&pd.counts, std::max<uint64_t>(ngroups, 1) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&pd.err, 4);
+  if (e != cudaSuccess) return fail(e);
+  pd.aips = p->aips;
+  if (n) e = cudaMemcpyAsync(p->aips, d_aips, n * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pd.err, 0, 4, st);
+  if (e == cudaSuccess) e = vbk::launch_plan_count(d, h->s, pd, st);
+  if (e == cudaSuccess && ngroups)
+    e = cudaMemcpyAsync(counts.data(), pd.counts, ngroups * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(e);
+  // group offsets, each group padded to whole uint4s of entries
+  unsigned long long run = 0;
+  for (uint64_t i = 0; i < ngroups; ++i) {
+    goff[i] = run;
+    run += (counts[i] + 3ull) & ~3ull;
+  }
+  goff[ngroups] = run;
+  p->n_entries = run;
+  e = cudaMalloc(&pd.entries, std::max<unsigned long long>(run, 4) * 4);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(pd.goff, goff.data(), (ngroups + 1) * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pd.entries, 0xff, std::max<unsigned long long>(run, 4) * 4, st);
+  if (e == cudaSuccess) e = vbk::launch_plan_fill(d, h->s, pd, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(e);
+  cudaFree(pd.counts);
+  pd.counts = nullptr;
+  p->bytes = std::max<uint64_t>(n, 1) * 4 + (ngroups + 1) * 8 + std::max<unsigned long long>(run, 4) * 4 + 4;
+  *out = p;
+  return VBDR_OK;
+}
+
+int vbdr_plan_destroy(vbdr_plan_t p) {
+  if (!p) return VBDR_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != p->device) cudaSetDevice(p->device);
+  cudaFree(p->aips);
+  cudaFree(p->dev.entries);
+  cudaFree(p->dev.goff);
+  cudaFree(p->dev.counts);
+  cudaFree(p->dev.err);
+  if (cur != p->device) cudaSetDevice(cur);
+  delete p;
+  return VBDR_OK;
+}
+
+int vbdr_plan_info(vbdr_plan_t p, uint64_t *n_hosts, uint64_t *n_entries, uint64_t *device_bytes) {
+  if (!p) return VBDR_EINVAL;
+  if (n_hosts) *n_hosts = p->dev.n;
+  if (n_entries) *n_entries = p->n_entries;
+  if (device_bytes) *device_bytes = p->bytes;
+  return VBDR_OK;
+}
+
+int vbdr_plan_status(vbdr_plan_t p) {
+  if (!p) return VBDR_EINVAL;
+  uint32_t err = 0;
+  if (cudaMemcpy(&err, p->dev.err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return VBDR_ECUDA;
+  }
+  return err ? VBDR_ETIMEOUT : VBDR_OK;
+}
+
+namespace {
+bool plan_matches(const vbdr *h, const vbdr_plan *p) {
+  return p->device == h->device && p->Z == h->d.Z && p->b == h->d.b && p->b_min == h->d.b_min &&
+         p->group_rule == h->d.group_rule && p->A0 == h->d.A0;
+}
+}  // namespace
+
+int vbdr_estimate_planned(vbdr_t h, vbdr_plan_t p, float *d_out, void *stream) {
+  if (!h || !p) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!plan_matches(h, p)) return VBDR_EINVAL;
+  if (!h->slid) return VBDR_EORDER;
+  if (p->dev.n == 0) return VBDR_OK;
+  if (!d_out || ((uintptr_t)d_out & 3u)) return VBDR_EINVAL;
+  return fail_cuda(h, vbk::launch_planned_estimate(h->d, h->s, h->est, p->dev, d_out,
+                                                   (cudaStream_t)stream));
+}
+
+int vbdr_estimate_planned_host(vbdr_t h, vbdr_plan_t p, float *h_out, void *stream) {
+  if (!h || !p) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!plan_matches(h, p)) return VBDR_EINVAL;
+  if (!h->slid) return VBDR_EORDER;
+  const uint64_t n = p->dev.n;
+  if (n == 0) return VBDR_OK;
+  if (!h_out) return VBDR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (n > h->est_cap) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    cudaFree(h->d_aips);
+    cudaFree(h->d_out);
+    h->d_aips = nullptr;
+    h->d_out = nullptr;
+    h->est_cap = 0;
+    if (cudaMalloc(&h->d_aips, n * 4) != cudaSuccess ||
+        cudaMalloc(&h->d_out, n * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return VBDR_ENOMEM;
+    }
+    h->est_cap = n;
+  }
+  e = vbk::launch_planned_estimate(h->d, h->s, h->est, p->dev, h->d_out, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, h->d_out, n * 4, cudaMemcpyDeviceToHost, st);
+  return fail_cuda(h, e);
 }
 
 }  // extern "C"

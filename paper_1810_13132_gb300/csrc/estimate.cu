@@ -64,14 +64,7 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
     for (uint32_t i = threadIdx.x; i < gmax; i += blockDim.x) kt_s[i] = s.ktab[i];
   }
   for (uint32_t i = threadIdx.x; i < (uint32_t)kLnTab; i += blockDim.x) lnv_s[i] = s.lnv[i];
-  if (threadIdx.x == 0) {
-    // pool noise term n_Z / Z from the sums of the last slide
-    const double Z = (double)d.Z;
-    const unsigned long long S_Z = s.sums[0], V_Z = s.sums[1];
-    double E = c.amm_Z / ldexp((double)S_Z, -32);
-    if (E <= 2.5 * Z && V_Z > 0) E = Z * log(Z / (double)V_Z);
-    nZZ_s = E / Z;
-  }
+  if (threadIdx.x == 0) nZZ_s = pool_noise(d, s, c);
   __syncthreads();
   const KEnt *kt = SMEM_KT ? kt_s : s.ktab;
   const double nZZ = nZZ_s;
@@ -171,12 +164,8 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
       const unsigned long long myS = resS[wib][lane];
       const uint32_t myV = resV[wib][lane];
       const uint32_t b = host_b(d, aip_l);
-      const double g = (double)(1u << b);
-      double n_g = c.amm[b] / ldexp((double)myS, -32);
-      if (n_g <= 2.5 * g && myV > 0)
-        n_g = g * (myV < (uint32_t)kLnTab ? c.lng[b] - lnv_s[myV] : log(g / (double)myV));
-      double est = c.kz[b] * (ldexp(n_g, -(int)b) - nZZ);
-      if (!(est > 0.0)) est = 0.0;
+      double n_g;
+      const double est = host_estimate(myS, myV, b, c, lnv_s, nZZ, &n_g);
       if constexpr (MODE == kPlain) {
         out[h_l] = (float)est;
       } else {

@@ -1,0 +1,277 @@
+// plan.cu -- planned estimate for a fixed host list (Sec. 4.1 Alg. 5 with
+// Alg. 3, evaluated register-chunk by register-chunk).
+//
+// The plain estimate (estimate.cu) gathers every virtual register of every
+// host from the byte array reg[Z]: H g random one-byte reads, bound by the
+// L2 random-sector rate.  The map from (host, virtual index i) to physical
+// BDR (Alg. 3) depends only on the host address, i and the handle's
+// configuration, so for a host list that is estimated again after every
+// slide it can be computed once.  A plan stores it sorted by register chunk
+// (2^15 BDRs, 32 KiB of reg):
+//
+//   hosts are cut into blocks of HB (<= 8000); for block blk and chunk c the
+//   group (blk, c) lists, for every virtual register of the block's hosts
+//   that Alg. 3 sends into chunk c, (local host << 15) | (pidx mod 2^15).
+//
+// The planned estimate runs one CTA per block: a producer warp streams reg
+// chunk by chunk into a 4-slot shared-memory ring with TMA bulk copies
+// (cp.async.bulk, completion on an mbarrier), 31 consumer warps walk the
+// group of the chunk in the ring, read each register from shared memory and
+// add its term to the host's exact sums with one shared atomic:
+//   M = 0      -> V   += 1                 (contributes 2^32 to S)
+//   M in 1..16 -> Shi += 2^(16 - M)        (2^(32-M) = Shi unit 2^16)
+//   M > 16     -> Slo += 2^(32 - M)
+// so S = V 2^32 + Shi 2^16 + Slo exactly (each field < 2^32 for g <= 2^16).
+// The sums are the same integers as the gather kernel's; the finish is the
+// same function (host_estimate), so both estimates agree bit for bit.
+//
+// Every wait on an mbarrier is bounded; a wait that expires sets the plan's
+// error word, the producer first waits (bounded) for its copies in flight,
+// and the block's outputs are written as NaN.
+#include "vbdr_internal.cuh"
+
+namespace vbk {
+namespace {
+
+constexpr int kPlanSlots = 4;
+constexpr int kConsumerWarps = 31;
+constexpr int kPlanThreads = (kConsumerWarps + 1) * 32;
+constexpr int kBuildThreads = 1024;
+constexpr uint32_t kChunkBytes = (uint32_t)kPlanChunk;
+constexpr uint32_t kWaitLimit = 1u << 21;  // try_wait rounds before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+// Wait for the phase of parity `parity` to complete; false after kWaitLimit
+// unsuccessful rounds.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
+               : "memory");
+}
+// TMA bulk copy global -> shared, completing `bytes` transactions on b.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(b))
+      : "memory");
+}
+__device__ __forceinline__ uint4 ld_stream(const uint4 *p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// Block blk's hosts: [blk HB, min((blk + 1) HB, n)).
+__device__ __forceinline__ uint32_t block_hosts(const PlanDev &p, uint32_t blk) {
+  const uint64_t h0 = (uint64_t)blk * p.HB;
+  const uint64_t left = p.n - h0;
+  return left < p.HB ? (uint32_t)left : p.HB;
+}
+
+// Building, pass 1: per block, the number of virtual registers that Alg. 3
+// sends into each chunk (shared counters, then one store per chunk).
+__global__ void __launch_bounds__(kBuildThreads)
+    plan_count_kernel(Dims d, DevState s, PlanDev p) {
+  extern __shared__ uint32_t cnt[];
+  const uint32_t blk = blockIdx.x;
+  for (uint32_t c = threadIdx.x; c < p.nchunks; c += blockDim.x) cnt[c] = 0;
+  __syncthreads();
+  const uint32_t nh = block_hosts(p, blk);
+  const uint32_t *aips = p.aips + (uint64_t)blk * p.HB;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  for (uint32_t h = warp; h < nh; h += warps) {
+    const uint32_t aip = aips[h];
+    const uint32_t g = 1u << host_b(d, aip);
+    for (uint32_t i = lane; i < g; i += 32) {
+      const uint32_t pidx = reduce32(hash32(aip, s.ktab[i]), d.zmul);
+      atomicAdd(&cnt[pidx >> kPlanChunkLog2], 1u);
+    }
+  }
+  __syncthreads();
+  for (uint32_t c = threadIdx.x; c < p.nchunks; c += blockDim.x)
+    p.counts[(uint64_t)blk * p.nchunks + c] = cnt[c];
+}
+
+// Building, pass 2: every virtual register takes the next free slot of its
+// group (the slot order within a group is immaterial: the sums are exact).
+__global__ void __launch_bounds__(kBuildThreads)
+    plan_fill_kernel(Dims d, DevState s, PlanDev p) {
+  extern __shared__ uint32_t cur[];
+  const uint32_t blk = blockIdx.x;
+  for (uint32_t c = threadIdx.x; c < p.nchunks; c += blockDim.x) cur[c] = 0;
+  __syncthreads();
+  const uint32_t nh = block_hosts(p, blk);
+  const uint32_t *aips = p.aips + (uint64_t)blk * p.HB;
+  const unsigned long long *goff = p.goff + (uint64_t)blk * p.nchunks;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  for (uint32_t h = warp; h < nh; h += warps) {
+    const uint32_t aip = aips[h];
+    const uint32_t g = 1u << host_b(d, aip);
+    for (uint32_t i = lane; i < g; i += 32) {
+      const uint32_t pidx = reduce32(hash32(aip, s.ktab[i]), d.zmul);
+      const uint32_t c = pidx >> kPlanChunkLog2;
+      const uint32_t slot = atomicAdd(&cur[c], 1u);
+      p.entries[goff[c] + slot] = (h << kPlanChunkLog2) | (pidx & (kChunkBytes - 1));
+    }
+  }
+}
+
+// Shared memory of the planned estimate.
+struct PlanSmem {
+  unsigned char ring[kPlanSlots][kChunkBytes];
+  uint32_t acc[3][kPlanMaxHB];  // V, Shi, Slo
+  uint64_t full[kPlanSlots], empty[kPlanSlots];
+  double nZZ;
+  int bad;
+};
+
+__device__ __forceinline__ void take(const unsigned char *ring, uint32_t (*acc)[kPlanMaxHB],
+                                     uint32_t e) {
+  if (e == kPlanSentinel) return;
+  const uint32_t M = ring[e & (kChunkBytes - 1)];
+  const uint32_t lh = e >> kPlanChunkLog2;
+  const uint32_t which = M == 0 ? 0u : (M <= 16 ? 1u : 2u);
+  const uint32_t val = M == 0 ? 1u : (M <= 16 ? 1u << (16 - M) : 1u << (32 - M));
+  atomicAdd(&acc[which][lh], val);
+}
+
+__global__ void __launch_bounds__(kPlanThreads, 1)
+    planned_estimate_kernel(Dims d, DevState s, EstConst c, PlanDev p, float *__restrict__ out) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  PlanSmem &S = *reinterpret_cast<PlanSmem *>(smem_raw);
+  const uint32_t blk = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t nh = block_hosts(p, blk);
+  for (uint32_t i = threadIdx.x; i < kPlanMaxHB; i += blockDim.x)
+    S.acc[0][i] = S.acc[1][i] = S.acc[2][i] = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kPlanSlots; ++i) {
+      mbar_init(&S.full[i], 1);
+      mbar_init(&S.empty[i], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    S.nZZ = pool_noise(d, s, c);
+    S.bad = 0;
+  }
+  __syncthreads();
+  const uint32_t nch = p.nchunks;
+  const unsigned long long *goff = p.goff + (uint64_t)blk * nch;
+  if (warp == kConsumerWarps) {
+    // producer: chunk c into slot c % 4 once the consumers released it
+    if (lane == 0) {
+      bool ok = true;
+      uint32_t issued = 0;
+      for (uint32_t ch = 0; ch < nch; ++ch) {
+        const uint32_t slot = ch % kPlanSlots;
+        if (ch >= (uint32_t)kPlanSlots && !mbar_wait(&S.empty[slot], (ch / kPlanSlots - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&S.full[slot], kChunkBytes);
+        bulk_load(S.ring[slot], s.reg + (uint64_t)ch * kChunkBytes, kChunkBytes, &S.full[slot]);
+        issued = ch + 1;
+      }
+      // every issued copy lands before the block may finish
+      const uint32_t first = issued > (uint32_t)kPlanSlots ? issued - kPlanSlots : 0u;
+      for (uint32_t ch = first; ch < issued; ++ch)
+        if (!mbar_wait(&S.full[ch % kPlanSlots], (ch / kPlanSlots) & 1u)) ok = false;
+      if (!ok) S.bad = 1;
+    }
+  } else {
+    const uint32_t t = threadIdx.x, T = kConsumerWarps * 32;
+    const uint4 none = make_uint4(kPlanSentinel, kPlanSentinel, kPlanSentinel, kPlanSentinel);
+    // the first uint4 of the next group is loaded one chunk ahead
+    auto first_of = [&](uint32_t ch) {
+      const uint64_t q = goff[ch] / 4 + t;
+      return q < goff[ch + 1] / 4 ? ld_stream(reinterpret_cast<const uint4 *>(p.entries) + q) : none;
+    };
+    uint4 cur = nch ? first_of(0) : none;
+    for (uint32_t ch = 0; ch < nch; ++ch) {
+      const uint32_t slot = ch % kPlanSlots;
+      const uint4 nxt = ch + 1 < nch ? first_of(ch + 1) : none;
+      if (!mbar_wait(&S.full[slot], (ch / kPlanSlots) & 1u)) {
+        S.bad = 1;
+        break;
+      }
+      const unsigned char *ring = S.ring[slot];
+      take(ring, S.acc, cur.x);
+      take(ring, S.acc, cur.y);
+      take(ring, S.acc, cur.z);
+      take(ring, S.acc, cur.w);
+      const uint4 *grp = reinterpret_cast<const uint4 *>(p.entries);
+      const uint64_t qend = goff[ch + 1] / 4;
+      for (uint64_t q = goff[ch] / 4 + t + T; q < qend; q += T) {
+        const uint4 e = ld_stream(grp + q);
+        take(ring, S.acc, e.x);
+        take(ring, S.acc, e.y);
+        take(ring, S.acc, e.z);
+        take(ring, S.acc, e.w);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.empty[slot]);
+      cur = nxt;
+    }
+  }
+  __syncthreads();
+  const bool bad = S.bad != 0;
+  if (bad && threadIdx.x == 0) atomicOr(p.err, 1u);
+  const double nZZ = S.nZZ;
+  const uint64_t h0 = (uint64_t)blk * p.HB;
+  for (uint32_t lh = threadIdx.x; lh < nh; lh += blockDim.x) {
+    const uint32_t V = S.acc[0][lh];
+    const unsigned long long Sum = ((unsigned long long)V << 32) +
+                                   ((unsigned long long)S.acc[1][lh] << 16) + S.acc[2][lh];
+    const uint32_t b = host_b(d, p.aips[h0 + lh]);
+    const double est = host_estimate(Sum, V, b, c, s.lnv, nZZ, nullptr);
+    out[h0 + lh] = bad ? __int_as_float(0x7fc00000) : (float)est;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_plan_count(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st) {
+  if (p.NB == 0) return cudaSuccess;
+  plan_count_kernel<<<p.NB, kBuildThreads, p.nchunks * sizeof(uint32_t), st>>>(d, s, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plan_fill(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st) {
+  if (p.NB == 0) return cudaSuccess;
+  plan_fill_kernel<<<p.NB, kBuildThreads, p.nchunks * sizeof(uint32_t), st>>>(d, s, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_planned_estimate(const Dims &d, const DevState &s, const EstConst &c,
+                                   const PlanDev &p, float *out, cudaStream_t st) {
+  if (p.NB == 0) return cudaSuccess;
+  const int smem = (int)sizeof(PlanSmem);
+  cudaError_t e = cudaFuncSetAttribute(planned_estimate_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  planned_estimate_kernel<<<p.NB, kPlanThreads, smem, st>>>(d, s, c, p, out);
+  return cudaGetLastError();
+}
+
+}  // namespace vbk

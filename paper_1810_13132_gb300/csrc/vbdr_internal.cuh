@@ -126,6 +126,35 @@ __device__ __forceinline__ uint32_t host_b(const Dims &d, uint32_t aip) {
   return d.group_rule ? d.b_min + (aip >> 30) : d.b;
 }
 
+// Pool noise term n_Z / Z of the estimator (Sec. 4.1) from the pool sums of
+// the last slide: HLL of the Z registers, small-range linear counting.
+__device__ __forceinline__ double pool_noise(const Dims &d, const DevState &s, const EstConst &c) {
+  const double Z = (double)d.Z;
+  const unsigned long long S_Z = s.sums[0], V_Z = s.sums[1];
+  double E = c.amm_Z / ldexp((double)S_Z, -32);
+  if (E <= 2.5 * Z && V_Z > 0) E = Z * log(Z / (double)V_Z);
+  return E / Z;
+}
+
+// Estimate of one host (log2 g = b) from the exact sums of its g virtual
+// registers, S = sum_i 2^(32 - M_i) and V = #{M_i = 0}:
+//   n_g = alpha_g g^2 / (S 2^-32), or g ln(g / V) when at most 2.5 g and
+//   V > 0;  n = max(0, Z g / (Z - g) * (n_g / g - nZZ)).
+// lnv: ln v for v < kLnTab.  Every kernel that estimates calls this, so
+// their results agree bit for bit.
+__device__ __forceinline__ double host_estimate(unsigned long long S, uint32_t V, uint32_t b,
+                                                const EstConst &c, const double *lnv, double nZZ,
+                                                double *n_g_out) {
+  const double g = (double)(1u << b);
+  double n_g = c.amm[b] / ldexp((double)S, -32);
+  if (n_g <= 2.5 * g && V > 0)
+    n_g = g * (V < (uint32_t)kLnTab ? c.lng[b] - lnv[V] : log(g / (double)V));
+  double est = c.kz[b] * (ldexp(n_g, -(int)b) - nZZ);
+  if (!(est > 0.0)) est = 0.0;
+  if (n_g_out) *n_g_out = n_g;
+  return est;
+}
+
 // ----- launchers (defined in the kernel translation units) -----
 cudaError_t launch_init(const Dims &d, const DevState &s, cudaStream_t st);
 cudaError_t launch_scan(const Dims &d, const DevState &s, int layout,
@@ -158,5 +187,32 @@ cudaError_t launch_load_virtual(const Dims &d, const DevState &s, const uint32_t
                                 cudaStream_t st);
 cudaError_t launch_pool_sums(const uint8_t *reg, uint64_t Z, unsigned long long *sums,
                              cudaStream_t st);
+
+// ----- estimate plans (plan.cu) -----
+// Register chunk of the planned estimate: 2^15 BDRs (32 KiB of reg); the
+// register array is allocated in whole chunks.
+constexpr int kPlanChunkLog2 = 15;
+constexpr uint64_t kPlanChunk = 1ull << kPlanChunkLog2;
+constexpr uint32_t kPlanMaxHB = 8000;       // hosts per block (shared accumulators)
+constexpr uint32_t kPlanMaxChunks = 8192;   // Z <= 2^28
+constexpr uint32_t kPlanSentinel = 0xffffffffu;
+// Device view of a plan: hosts [blk HB, (blk + 1) HB) form block blk; the
+// entries of group (blk, c) -- one per virtual register of the block's hosts
+// that Alg. 3 maps into chunk c, (local host << 15) | (pidx mod 2^15) --
+// occupy [goff[blk nchunks + c], goff[blk nchunks + c + 1]), padded with
+// kPlanSentinel to a multiple of 4.
+struct PlanDev {
+  const uint32_t *aips;     // [n]
+  uint32_t *entries;        // [goff[NB nchunks]]
+  unsigned long long *goff; // [NB nchunks + 1]
+  uint32_t *counts;         // [NB nchunks] (building)
+  uint32_t *err;            // bounded-wait failures
+  uint64_t n;
+  uint32_t HB, NB, nchunks;
+};
+cudaError_t launch_plan_count(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st);
+cudaError_t launch_plan_fill(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st);
+cudaError_t launch_planned_estimate(const Dims &d, const DevState &s, const EstConst &c,
+                                   const PlanDev &p, float *out, cudaStream_t st);
 
 }  // namespace vbk

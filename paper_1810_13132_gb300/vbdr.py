@@ -45,6 +45,13 @@ _SIGS = {
     "vbdr_slide": (ctypes.c_int, [_VP, _VP]),
     "vbdr_estimate": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
     "vbdr_estimate_host": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
+    "vbdr_plan_create": (ctypes.c_int, [_VP, _VP, _U64, ctypes.POINTER(_VP), _VP]),
+    "vbdr_plan_destroy": (ctypes.c_int, [_VP]),
+    "vbdr_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64),
+                                      ctypes.POINTER(_U64)]),
+    "vbdr_plan_status": (ctypes.c_int, [_VP]),
+    "vbdr_estimate_planned": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "vbdr_estimate_planned_host": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "vbdr_get_dims": (ctypes.c_int, [_VP, ctypes.POINTER(_U32), ctypes.POINTER(_U32),
                                      ctypes.POINTER(_U32)]),
     "vbdr_copy_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
@@ -217,6 +224,32 @@ class Vbdr:
         _check("vbdr_estimate_host", self._L.vbdr_estimate_host(
             self._h, pa, n, po, _stream_ptr(stream)))
 
+    # -- planned estimation ----------------------------------------------------
+    def plan(self, aips, stream=None) -> "Plan":
+        """Estimate plan of a host list (int32/uint32 CUDA tensor); see Plan."""
+        assert aips.is_cuda and aips.is_contiguous()
+        n = aips.numel()
+        p = ctypes.c_void_p()
+        _check("vbdr_plan_create", self._L.vbdr_plan_create(
+            self._h, aips.data_ptr() if n else None, n, ctypes.byref(p), _stream_ptr(stream)))
+        return Plan(self._L, p, n)
+
+    def estimate_planned(self, plan: "Plan", out=None, stream=None):
+        """Estimates of the plan's hosts (float32 CUDA tensor, plan order)."""
+        import torch
+        if out is None:
+            out = torch.empty(plan.n_hosts, dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.numel() >= plan.n_hosts
+        _check("vbdr_estimate_planned", self._L.vbdr_estimate_planned(
+            self._h, plan._p, out.data_ptr() if plan.n_hosts else None, _stream_ptr(stream)))
+        return out
+
+    def estimate_planned_host(self, plan: "Plan", out, stream=None) -> None:
+        po, n = _host_ptr(out, 1)
+        assert n >= plan.n_hosts
+        _check("vbdr_estimate_planned_host", self._L.vbdr_estimate_planned_host(
+            self._h, plan._p, po, _stream_ptr(stream)))
+
     # -- batched estimation --------------------------------------------------------
     def load_virtual_registers(self, aips, offsets, vregs, stream=None) -> None:
         """Register-level state (device tensors: int32 aips, int64 offsets,
@@ -292,6 +325,36 @@ class Vbdr:
         _check("vbdr_copy_pool_sums", self._L.vbdr_copy_pool_sums(
             self._h, ctypes.byref(S), ctypes.byref(V), _stream_ptr(stream)))
         return S.value, V.value
+
+
+class Plan:
+    """A host list's map from virtual to physical registers, grouped by
+    register chunk, for ``Vbdr.estimate_planned`` (see include/vbdr.h).
+    Valid for every handle of the same configuration on the same device."""
+
+    def __init__(self, L, p, n_hosts: int):
+        self._L, self._p, self.n_hosts = L, p, n_hosts
+
+    def info(self) -> dict:
+        n, e, b = _U64(), _U64(), _U64()
+        _check("vbdr_plan_info", self._L.vbdr_plan_info(self._p, ctypes.byref(n), ctypes.byref(e),
+                                                        ctypes.byref(b)))
+        return {"hosts": n.value, "entries": e.value, "device_bytes": b.value}
+
+    def status(self) -> None:
+        """Raise VbdrError if a bounded wait of an earlier estimate expired."""
+        _check("vbdr_plan_status", self._L.vbdr_plan_status(self._p))
+
+    def close(self) -> None:
+        if getattr(self, "_p", None):
+            self._L.vbdr_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class server_config(ctypes.Structure):
