@@ -701,7 +701,6 @@ int vbdr_plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n, vbdr_plan_t *
   e = cudaMalloc(&pd.entries, std::max<unsigned long long>(run, 4) * 4);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(pd.goff, goff.data(), (ngroups + 1) * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(pd.entries, 0xff, std::max<unsigned long long>(run, 4) * 4, st);
   if (e == cudaSuccess) e = vbk::launch_plan_fill(d, h->s, pd, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(e);

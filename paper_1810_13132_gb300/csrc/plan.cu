@@ -11,7 +11,8 @@
 //
 //   hosts are cut into blocks of HB (<= 8000); for block blk and chunk c the
 //   group (blk, c) lists, for every virtual register of the block's hosts
-//   that Alg. 3 sends into chunk c, (local host << 15) | (pidx mod 2^15).
+//   that Alg. 3 sends into chunk c, (local host << 15) | (pidx mod 2^15);
+//   groups are padded to whole uint4s with entries of a spare host slot.
 //
 // The planned estimate runs one CTA per block: a producer warp streams reg
 // chunk by chunk into a 4-slot shared-memory ring with TMA bulk copies
@@ -25,9 +26,9 @@
 // The sums are the same integers as the gather kernel's; the finish is the
 // same function (host_estimate), so both estimates agree bit for bit.
 //
-// Every wait on an mbarrier is bounded; a wait that expires sets the plan's
-// error word, the producer first waits (bounded) for its copies in flight,
-// and the block's outputs are written as NaN.
+// Every wait on an mbarrier is bounded (0.2 s of %globaltimer); a wait that
+// expires sets the plan's error word, the producer first waits (bounded) for
+// its copies in flight, and the block's outputs are written as NaN.
 #include "vbdr_internal.cuh"
 
 namespace vbk {
@@ -35,10 +36,12 @@ namespace {
 
 constexpr int kPlanSlots = 4;
 constexpr int kConsumerWarps = 31;
+constexpr int kPrefetch = 2;  // chunks of entries each consumer thread has in flight
 constexpr int kPlanThreads = (kConsumerWarps + 1) * 32;
 constexpr int kBuildThreads = 1024;
 constexpr uint32_t kChunkBytes = (uint32_t)kPlanChunk;
-constexpr uint32_t kWaitLimit = 1u << 21;  // try_wait rounds before giving up
+constexpr uint64_t kWaitLimitNs = 200000000ull;  // 0.2 s: a wait this long is a failure
+constexpr uint32_t kSuspendNs = 20000;           // suspend hint of one try_wait round
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -46,19 +49,30 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
 }
-// Wait for the phase of parity `parity` to complete; false after kWaitLimit
-// unsuccessful rounds.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(b)), "r"(parity), "n"(kSuspendNs)
+      : "memory");
+  return done != 0;
+}
+// Wait for the phase of parity `parity` to complete.  Each round may park
+// the warp (suspend hint) instead of spinning on the shared-memory pipe;
+// false once the wait has lasted kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_addr(b)), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = global_ns();
+  do {
+    if (mbar_try(b, parity)) return true;
+  } while (global_ns() - t0 < kWaitLimitNs);
   return false;
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
@@ -137,25 +151,32 @@ __global__ void __launch_bounds__(kBuildThreads)
       p.entries[goff[c] + slot] = (h << kPlanChunkLog2) | (pidx & (kChunkBytes - 1));
     }
   }
+  __syncthreads();
+  // the group's padding: entries of the spare host slot kPlanMaxHB
+  for (uint32_t c = threadIdx.x; c < p.nchunks; c += blockDim.x)
+    for (unsigned long long q = goff[c] + cur[c]; q < goff[c + 1]; ++q) p.entries[q] = kPlanPad;
 }
 
 // Shared memory of the planned estimate.
+constexpr uint32_t kAccRow = kPlanMaxHB + 1;  // + the spare slot of padding entries
 struct PlanSmem {
   unsigned char ring[kPlanSlots][kChunkBytes];
-  uint32_t acc[3][kPlanMaxHB];  // V, Shi, Slo
+  uint32_t acc[3][kAccRow];  // V, Shi, Slo
   uint64_t full[kPlanSlots], empty[kPlanSlots];
   double nZZ;
   int bad;
 };
 
-__device__ __forceinline__ void take(const unsigned char *ring, uint32_t (*acc)[kPlanMaxHB],
-                                     uint32_t e) {
-  if (e == kPlanSentinel) return;
+// One entry: register M of the chunk in the ring, added to its host's sums.
+// which = (M + 15) >> 4 picks V (M = 0), Shi (1..16) or Slo (17..32), and
+// 1 << ((16 - M) & 15) is 1, 2^(16-M) or 2^(32-M) respectively.
+// The two min() keep every access inside the accumulators whatever the
+// entry or register value.
+__device__ __forceinline__ void take(const unsigned char *ring, uint32_t *acc, uint32_t e) {
   const uint32_t M = ring[e & (kChunkBytes - 1)];
-  const uint32_t lh = e >> kPlanChunkLog2;
-  const uint32_t which = M == 0 ? 0u : (M <= 16 ? 1u : 2u);
-  const uint32_t val = M == 0 ? 1u : (M <= 16 ? 1u << (16 - M) : 1u << (32 - M));
-  atomicAdd(&acc[which][lh], val);
+  const uint32_t which = min((M + 15u) >> 4, 2u);
+  const uint32_t lh = min(e >> kPlanChunkLog2, kPlanMaxHB);
+  atomicAdd(acc + which * kAccRow + lh, 1u << ((16u - M) & 15u));
 }
 
 __global__ void __launch_bounds__(kPlanThreads, 1)
@@ -164,7 +185,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   PlanSmem &S = *reinterpret_cast<PlanSmem *>(smem_raw);
   const uint32_t blk = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t nh = block_hosts(p, blk);
-  for (uint32_t i = threadIdx.x; i < kPlanMaxHB; i += blockDim.x)
+  for (uint32_t i = threadIdx.x; i < kAccRow; i += blockDim.x)
     S.acc[0][i] = S.acc[1][i] = S.acc[2][i] = 0;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kPlanSlots; ++i) {
@@ -202,36 +223,50 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   } else {
     const uint32_t t = threadIdx.x, T = kConsumerWarps * 32;
     const uint4 none = make_uint4(kPlanSentinel, kPlanSentinel, kPlanSentinel, kPlanSentinel);
-    // the first uint4 of the next group is loaded one chunk ahead
+    // each thread's first uint4 of a group is loaded kPrefetch chunks
+    // ahead (the plan stream comes from DRAM; one chunk of work does not
+    // cover its latency)
+    // thread t takes uint4 (t + 160 ch) mod T of group ch and then every
+    // T-th: the threads left without work by a group smaller than T move
+    // by five warps from chunk to chunk, so no warp idles more than others
+    auto lead = [&](uint32_t ch) { return (t + 160u * ch) % T; };
     auto first_of = [&](uint32_t ch) {
-      const uint64_t q = goff[ch] / 4 + t;
+      if (ch >= nch) return none;
+      const uint64_t q = goff[ch] / 4 + lead(ch);
       return q < goff[ch + 1] / 4 ? ld_stream(reinterpret_cast<const uint4 *>(p.entries) + q) : none;
     };
-    uint4 cur = nch ? first_of(0) : none;
+    uint4 pf[kPrefetch];
+#pragma unroll
+    for (int i = 0; i < kPrefetch; ++i) pf[i] = first_of(i);
     for (uint32_t ch = 0; ch < nch; ++ch) {
       const uint32_t slot = ch % kPlanSlots;
-      const uint4 nxt = ch + 1 < nch ? first_of(ch + 1) : none;
+      const uint4 cur = pf[0];
+#pragma unroll
+      for (int i = 0; i + 1 < kPrefetch; ++i) pf[i] = pf[i + 1];
+      pf[kPrefetch - 1] = first_of(ch + kPrefetch);
       if (!mbar_wait(&S.full[slot], (ch / kPlanSlots) & 1u)) {
         S.bad = 1;
         break;
       }
       const unsigned char *ring = S.ring[slot];
-      take(ring, S.acc, cur.x);
-      take(ring, S.acc, cur.y);
-      take(ring, S.acc, cur.z);
-      take(ring, S.acc, cur.w);
+      uint32_t *acc = &S.acc[0][0];
+      if (cur.x != kPlanSentinel) {
+        take(ring, acc, cur.x);
+        take(ring, acc, cur.y);
+        take(ring, acc, cur.z);
+        take(ring, acc, cur.w);
+      }
       const uint4 *grp = reinterpret_cast<const uint4 *>(p.entries);
       const uint64_t qend = goff[ch + 1] / 4;
-      for (uint64_t q = goff[ch] / 4 + t + T; q < qend; q += T) {
+      for (uint64_t q = goff[ch] / 4 + lead(ch) + T; q < qend; q += T) {
         const uint4 e = ld_stream(grp + q);
-        take(ring, S.acc, e.x);
-        take(ring, S.acc, e.y);
-        take(ring, S.acc, e.z);
-        take(ring, S.acc, e.w);
+        take(ring, acc, e.x);
+        take(ring, acc, e.y);
+        take(ring, acc, e.z);
+        take(ring, acc, e.w);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.empty[slot]);
-      cur = nxt;
     }
   }
   __syncthreads();

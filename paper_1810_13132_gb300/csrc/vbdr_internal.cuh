@@ -195,12 +195,13 @@ constexpr int kPlanChunkLog2 = 15;
 constexpr uint64_t kPlanChunk = 1ull << kPlanChunkLog2;
 constexpr uint32_t kPlanMaxHB = 8000;       // hosts per block (shared accumulators)
 constexpr uint32_t kPlanMaxChunks = 8192;   // Z <= 2^28
-constexpr uint32_t kPlanSentinel = 0xffffffffu;
+constexpr uint32_t kPlanSentinel = 0xffffffffu;         // no entry (never stored)
+constexpr uint32_t kPlanPad = kPlanMaxHB << kPlanChunkLog2;  // padding: spare host slot
 // Device view of a plan: hosts [blk HB, (blk + 1) HB) form block blk; the
 // entries of group (blk, c) -- one per virtual register of the block's hosts
 // that Alg. 3 maps into chunk c, (local host << 15) | (pidx mod 2^15) --
 // occupy [goff[blk nchunks + c], goff[blk nchunks + c + 1]), padded with
-// kPlanSentinel to a multiple of 4.
+// kPlanPad to a multiple of 4.
 struct PlanDev {
   const uint32_t *aips;     // [n]
   uint32_t *entries;        // [goff[NB nchunks]]
