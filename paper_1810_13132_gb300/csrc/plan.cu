@@ -9,16 +9,17 @@
 // slide it can be computed once.  A plan stores it sorted by register chunk
 // (2^15 BDRs, 32 KiB of reg):
 //
-//   hosts are cut into blocks of HB (<= 8000); for block blk and chunk c the
+//   hosts are cut into blocks of HB (<= 7000); for block blk and chunk c the
 //   group (blk, c) lists, for every virtual register of the block's hosts
 //   that Alg. 3 sends into chunk c, (local host << 15) | (pidx mod 2^15);
 //   groups are padded to whole uint4s with entries of a spare host slot.
 //
 // The planned estimate runs one CTA per block: a producer warp streams reg
-// chunk by chunk into a 4-slot shared-memory ring with TMA bulk copies
-// (cp.async.bulk, completion on an mbarrier), 31 consumer warps walk the
-// group of the chunk in the ring, read each register from shared memory and
-// add its term to the host's exact sums with one shared atomic:
+// chunk by chunk, together with the chunk's group of entries, into a 3-slot
+// shared-memory ring with TMA bulk copies (cp.async.bulk, completion on an
+// mbarrier); 31 consumer warps walk the staged group, read each register
+// from shared memory and add its term to the host's exact sums with one
+// shared atomic:
 //   M = 0      -> V   += 1                 (contributes 2^32 to S)
 //   M in 1..16 -> Shi += 2^(16 - M)        (2^(32-M) = Shi unit 2^16)
 //   M > 16     -> Slo += 2^(32 - M)
@@ -34,9 +35,9 @@
 namespace vbk {
 namespace {
 
-constexpr int kPlanSlots = 4;
+constexpr int kPlanSlots = 3;
+constexpr uint32_t kEntCap = 4096;  // entries of a group staged in shared memory
 constexpr int kConsumerWarps = 31;
-constexpr int kPrefetch = 2;  // chunks of entries each consumer thread has in flight
 constexpr int kPlanThreads = (kConsumerWarps + 1) * 32;
 constexpr int kBuildThreads = 1024;
 constexpr uint32_t kChunkBytes = (uint32_t)kPlanChunk;
@@ -161,11 +162,14 @@ __global__ void __launch_bounds__(kBuildThreads)
 constexpr uint32_t kAccRow = kPlanMaxHB + 1;  // + the spare slot of padding entries
 struct PlanSmem {
   unsigned char ring[kPlanSlots][kChunkBytes];
+  uint4 ents[kPlanSlots][kEntCap / 4];  // the group's first kEntCap entries
   uint32_t acc[3][kAccRow];  // V, Shi, Slo
   uint64_t full[kPlanSlots], empty[kPlanSlots];
   double nZZ;
   int bad;
 };
+
+static_assert(sizeof(PlanSmem) <= 227 * 1024, "shared memory of one CTA");
 
 // One entry: register M of the chunk in the ring, added to its host's sums.
 // which = (M + 15) >> 4 picks V (M = 0), Shi (1..16) or Slo (17..32), and
@@ -200,7 +204,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   const uint32_t nch = p.nchunks;
   const unsigned long long *goff = p.goff + (uint64_t)blk * nch;
   if (warp == kConsumerWarps) {
-    // producer: chunk c into slot c % 4 once the consumers released it
+    // producer: chunk c and its entries into slot c % 3 once the consumers
+    // released it
     if (lane == 0) {
       bool ok = true;
       uint32_t issued = 0;
@@ -210,8 +215,11 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
           ok = false;
           break;
         }
-        mbar_expect_tx(&S.full[slot], kChunkBytes);
+        const unsigned long long ne = goff[ch + 1] - goff[ch];
+        const uint32_t ebytes = 4u * (uint32_t)(ne < kEntCap ? ne : kEntCap);
+        mbar_expect_tx(&S.full[slot], kChunkBytes + ebytes);
         bulk_load(S.ring[slot], s.reg + (uint64_t)ch * kChunkBytes, kChunkBytes, &S.full[slot]);
+        if (ebytes) bulk_load(S.ents[slot], p.entries + goff[ch], ebytes, &S.full[slot]);
         issued = ch + 1;
       }
       // every issued copy lands before the block may finish
@@ -222,43 +230,30 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     }
   } else {
     const uint32_t t = threadIdx.x, T = kConsumerWarps * 32;
-    const uint4 none = make_uint4(kPlanSentinel, kPlanSentinel, kPlanSentinel, kPlanSentinel);
-    // each thread's first uint4 of a group is loaded kPrefetch chunks
-    // ahead (the plan stream comes from DRAM; one chunk of work does not
-    // cover its latency)
-    // thread t takes uint4 (t + 160 ch) mod T of group ch and then every
-    // T-th: the threads left without work by a group smaller than T move
-    // by five warps from chunk to chunk, so no warp idles more than others
-    auto lead = [&](uint32_t ch) { return (t + 160u * ch) % T; };
-    auto first_of = [&](uint32_t ch) {
-      if (ch >= nch) return none;
-      const uint64_t q = goff[ch] / 4 + lead(ch);
-      return q < goff[ch + 1] / 4 ? ld_stream(reinterpret_cast<const uint4 *>(p.entries) + q) : none;
-    };
-    uint4 pf[kPrefetch];
-#pragma unroll
-    for (int i = 0; i < kPrefetch; ++i) pf[i] = first_of(i);
+    uint32_t *acc = &S.acc[0][0];
     for (uint32_t ch = 0; ch < nch; ++ch) {
       const uint32_t slot = ch % kPlanSlots;
-      const uint4 cur = pf[0];
-#pragma unroll
-      for (int i = 0; i + 1 < kPrefetch; ++i) pf[i] = pf[i + 1];
-      pf[kPrefetch - 1] = first_of(ch + kPrefetch);
       if (!mbar_wait(&S.full[slot], (ch / kPlanSlots) & 1u)) {
         S.bad = 1;
         break;
       }
       const unsigned char *ring = S.ring[slot];
-      uint32_t *acc = &S.acc[0][0];
-      if (cur.x != kPlanSentinel) {
-        take(ring, acc, cur.x);
-        take(ring, acc, cur.y);
-        take(ring, acc, cur.z);
-        take(ring, acc, cur.w);
+      const uint64_t q0 = goff[ch] / 4, nq = goff[ch + 1] / 4 - q0;
+      const uint32_t nq_s = nq < kEntCap / 4 ? (uint32_t)nq : kEntCap / 4;
+      // thread t starts at uint4 (t + 160 ch) mod T: the threads left
+      // without work by a group smaller than T move by five warps from
+      // chunk to chunk, so no warp idles more than others
+      const uint32_t lead = (t + 160u * ch) % T;
+      for (uint32_t q = lead; q < nq_s; q += T) {
+        const uint4 e = S.ents[slot][q];
+        take(ring, acc, e.x);
+        take(ring, acc, e.y);
+        take(ring, acc, e.z);
+        take(ring, acc, e.w);
       }
-      const uint4 *grp = reinterpret_cast<const uint4 *>(p.entries);
-      const uint64_t qend = goff[ch + 1] / 4;
-      for (uint64_t q = goff[ch] / 4 + lead(ch) + T; q < qend; q += T) {
+      // a group larger than the staging slot: the rest from global memory
+      const uint4 *grp = reinterpret_cast<const uint4 *>(p.entries) + q0;
+      for (uint64_t q = nq_s + lead; q < nq; q += T) {
         const uint4 e = ld_stream(grp + q);
         take(ring, acc, e.x);
         take(ring, acc, e.y);

@@ -193,7 +193,7 @@ cudaError_t launch_pool_sums(const uint8_t *reg, uint64_t Z, unsigned long long 
 // register array is allocated in whole chunks.
 constexpr int kPlanChunkLog2 = 15;
 constexpr uint64_t kPlanChunk = 1ull << kPlanChunkLog2;
-constexpr uint32_t kPlanMaxHB = 8000;       // hosts per block (shared accumulators)
+constexpr uint32_t kPlanMaxHB = 7000;       // hosts per block (shared accumulators)
 constexpr uint32_t kPlanMaxChunks = 8192;   // Z <= 2^28
 constexpr uint32_t kPlanSentinel = 0xffffffffu;         // no entry (never stored)
 constexpr uint32_t kPlanPad = kPlanMaxHB << kPlanChunkLog2;  // padding: spare host slot
