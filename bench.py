@@ -481,6 +481,17 @@ def run_batched(a):
     est = out.cpu().numpy().astype(np.float64)
     rel = np.abs(est - br.card) / br.card
     gathers = int(br.g.sum())
+    # the same hosts through a plan (built once for the host list)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    plan = v.plan(aips)
+    torch.cuda.synchronize()
+    plan_info = dict(plan.info(), build_ms=round((time.perf_counter() - w0) * 1e3, 2))
+    out_p = torch.empty(H, dtype=torch.float32, device="cuda")
+    planned_ms = timed(lambda: v.estimate_planned(plan, out=out_p))
+    plan.status()
+    planned_same = bool(torch.equal(out_p.view(torch.int32), out.view(torch.int32)))
+    plan.close()
     line = {
         "metric": "batched estimate: hosts/s (one persistent autotuned launch)",
         "value": round(H / (tuned_ms * 1e-3) / 1e6, 2), "unit": "M hosts/s",
@@ -494,6 +505,8 @@ def run_batched(a):
         "per_group_launches_ms": round(per_group_ms, 4),
         "speedup_vs_per_group": round(per_group_ms / tuned_ms, 3),
         "gathers_per_s": round(gathers / (tuned_ms * 1e-3) / 1e9, 2),
+        "planned_ms": round(planned_ms, 4), "planned_equals_gather": planned_same,
+        "plan": plan_info,
         "accuracy": {"mre_vs_truth": float(rel.mean()), "median_rel_err": float(np.median(rel))},
         "gpu_launches": a.steps,
         "clocks": clk.summary(),
