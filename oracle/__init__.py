@@ -100,6 +100,17 @@ def lib() -> ctypes.CDLL:
         L.orc_vhll.argtypes = [ctypes.c_double, ctypes.c_double,
                                ctypes.c_uint64, ctypes.c_uint64,
                                ctypes.c_uint64, ctypes.c_uint64]
+        L.orc_loglog_alpha.restype = ctypes.c_double
+        L.orc_loglog_alpha.argtypes = [ctypes.c_double]
+        L.orc_loglog.restype = ctypes.c_double
+        L.orc_loglog.argtypes = [ctypes.c_double, ctypes.c_uint64]
+        L.orc_pcsa.restype = ctypes.c_double
+        L.orc_pcsa.argtypes = [ctypes.c_double, ctypes.c_uint64]
+        L.orc_estimate_alt.restype = ctypes.c_int
+        L.orc_estimate_alt.argtypes = [ctypes.c_void_p, ctypes.c_int, u32p, ctypes.c_uint64,
+                                       f64p]
+        L.orc_pool_sums_alt.argtypes = [ctypes.c_void_p, u64p, u64p]
+        L.orc_get_pcsa.argtypes = [ctypes.c_void_p, u8p]
         L.orc_table1_bits.restype = ctypes.c_uint32
         L.orc_table1_bits.argtypes = [ctypes.c_void_p, ctypes.c_int]
         _lib = L
@@ -133,6 +144,21 @@ def hll_alpha(m: float) -> float:
 
 def vhll(Z: float, g: float, S: int, V: int, S_Z: int, V_Z: int) -> float:
     return lib().orc_vhll(float(Z), float(g), int(S), int(V), int(S_Z), int(V_Z))
+
+
+def loglog_alpha(m: float) -> float:
+    return lib().orc_loglog_alpha(float(m))
+
+
+def loglog(m: float, L: int) -> float:
+    return lib().orc_loglog(float(m), int(L))
+
+
+def pcsa(m: float, P: int) -> float:
+    return lib().orc_pcsa(float(m), int(P))
+
+
+ESTIMATORS = {"loglog": 1, "pcsa": 2}
 
 
 class Oracle:
@@ -194,6 +220,29 @@ class Oracle:
         if rc != 0:
             raise RuntimeError("estimate before the first slide")
         return out
+
+    def estimate_alt(self, aips: np.ndarray, estimator: str) -> np.ndarray:
+        """LogLog ("loglog") or PCSA ("pcsa", gsmall only) estimates."""
+        aips = np.ascontiguousarray(aips, dtype=np.uint32)
+        out = np.empty(aips.shape[0], dtype=np.float64)
+        rc = lib().orc_estimate_alt(self._h, ESTIMATORS[estimator], _ptr(aips, ctypes.c_uint32),
+                                    aips.shape[0], _ptr(out, ctypes.c_double))
+        if rc == -1:
+            raise RuntimeError("estimate before the first slide")
+        if rc == -2:
+            raise ValueError("PCSA needs the gsmall layout")
+        return out
+
+    def pcsa_statistics(self) -> np.ndarray:
+        out = np.empty(self.Z, dtype=np.uint8)
+        lib().orc_get_pcsa(self._h, _ptr(out, ctypes.c_uint8))
+        return out
+
+    def pool_sums_alt(self) -> tuple[int, int]:
+        """(sum of registers, sum of PCSA statistics) over the pool."""
+        L, P = ctypes.c_uint64(), ctypes.c_uint64()
+        lib().orc_pool_sums_alt(self._h, ctypes.byref(L), ctypes.byref(P))
+        return L.value, P.value
 
     def features(self, aips: np.ndarray):
         """(X [n, 80] float64, n_plain [n]) of the learned correction."""

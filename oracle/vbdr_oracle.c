@@ -47,6 +47,19 @@
  *               estimate of all Z physical registers, each with HLL's
  *               small-range linear counting; clamped at 0.  The harmonic
  *               sums are exact integers S = sum 2^(32 - M).
+ *   LogLog /  : Sec. 4.1 notes that the BDR pool can serve PCSA and LogLog
+ *   PCSA        counting too.  LogLog (Durand & Flajolet 2003) reads the same
+ *               registers (Alg. 5's sum of LBP1 is its statistic):
+ *               n_m = alpha_m m 2^(sum M / m), alpha_m =
+ *               (Gamma(-1/m) (1 - 2^(1/m)) / ln 2)^(-m).  PCSA (Flajolet &
+ *               Martin 1985) keeps a bitmap per BDR: position r is set in the
+ *               window iff DR[r] is active, and the BDR's statistic R_j is
+ *               the index of its lowest unset position (r - 1 for the first
+ *               inactive r, R if all are active); n_m = (m / 0.77351)
+ *               2^(sum R_j / m).  Only gsmall records every LBP1 seen (Alg.
+ *               9); gfast and serial record a slice maximum, so PCSA reads
+ *               gsmall.  Both take the same virtual-sharing noise removal
+ *               as vHLL.
  *   mixed g   : the paper gives every host the same g.  For workloads with
  *               mixed g, group_rule 1 assigns host aip  b = b_min + (aip >> 30):
  *               four groups g = 2^b_min .. 2^(b_min+3) selected by the top two
@@ -115,7 +128,9 @@ typedef struct {
   uint32_t *bs;         /* [Z] bsLBP1 (gfast)                            */
   uint8_t *now;         /* [Z] nowLBP1 (serial)                          */
   uint8_t *reg;         /* [Z] register value of every physical BDR      */
+  uint8_t *pcsa;        /* [Z] PCSA statistic of every physical BDR      */
   uint64_t S_Z, V_Z;    /* pool sums of the last slide                   */
+  uint64_t L_Z, P_Z;    /* pool sums of registers and PCSA statistics    */
   uint64_t slices_closed;
 } orc_t;
 
@@ -152,8 +167,9 @@ orc_t *orc_create(int variant, uint32_t k, uint64_t Z, uint32_t b_default,
   o->bs = (uint32_t *)calloc((size_t)Z, sizeof(uint32_t));
   o->now = (uint8_t *)calloc((size_t)Z, 1);
   o->reg = (uint8_t *)calloc((size_t)Z, 1);
-  if (!o->DR || !o->bs || !o->now || !o->reg) {
-    free(o->DR); free(o->bs); free(o->now); free(o->reg); free(o);
+  o->pcsa = (uint8_t *)calloc((size_t)Z, 1);
+  if (!o->DR || !o->bs || !o->now || !o->reg || !o->pcsa) {
+    free(o->DR); free(o->bs); free(o->now); free(o->reg); free(o->pcsa); free(o);
     return NULL;
   }
   /* InitDR on every DR (Sec. 3): value 2^w - 1. */
@@ -163,7 +179,7 @@ orc_t *orc_create(int variant, uint32_t k, uint64_t Z, uint32_t b_default,
 
 void orc_destroy(orc_t *o) {
   if (!o) return;
-  free(o->DR); free(o->bs); free(o->now); free(o->reg); free(o);
+  free(o->DR); free(o->bs); free(o->now); free(o->reg); free(o->pcsa); free(o);
 }
 
 uint32_t orc_dr_max(const orc_t *o) { return o->dr_max; }
@@ -213,6 +229,15 @@ static uint32_t GetLBP1BDR(const orc_t *o, uint64_t j) {
   return 0;
 }
 
+/* PCSA statistic of a BDR's window bitmap (position r set iff DR[r] is
+ * active): the index of the lowest unset position, counted from 0. */
+static uint32_t PcsaBDR(const orc_t *o, uint64_t j) {
+  const uint8_t *drv = o->DR + j * (o->R + 1);
+  for (uint32_t r = 1; r <= o->R; ++r)
+    if (!IsActiveDR(o, drv[r])) return r - 1;
+  return o->R;
+}
+
 /* ------------------------------------------------------------ the scan */
 
 /* One time slice of pairs, AoS (aip, bip), in input order.
@@ -235,13 +260,17 @@ void orc_scan(orc_t *o, const uint32_t *pairs, uint64_t n) {
 }
 
 static void orc_pool_sums(orc_t *o) {
-  uint64_t S = 0, V = 0;
+  uint64_t S = 0, V = 0, L = 0, P = 0;
   for (uint64_t j = 0; j < o->Z; ++j) {
     S += 1ULL << (32 - o->reg[j]);
     V += (o->reg[j] == 0);
+    L += o->reg[j];
+    P += o->pcsa[j];
   }
   o->S_Z = S;
   o->V_Z = V;
+  o->L_Z = L;
+  o->P_Z = P;
 }
 
 /* Slice boundary.
@@ -256,6 +285,7 @@ void orc_slide(orc_t *o) {
     uint8_t *drv = orc_drv(o, j);
     if (o->variant == ORC_GSMALL) {
       o->reg[j] = (uint8_t)GetLBP1BDR(o, j);
+      o->pcsa[j] = (uint8_t)PcsaBDR(o, j);
       for (uint32_t r = 1; r <= o->R; ++r) SlideDR(o, &drv[r]);
       continue;
     }
@@ -271,6 +301,7 @@ void orc_slide(orc_t *o) {
     }
     if (lbp1 > 0) SetDR(&drv[lbp1]);
     o->reg[j] = (uint8_t)GetLBP1BDR(o, j);
+    /* a slice maximum is no bitmap: no PCSA statistic outside gsmall */
   }
   orc_pool_sums(o);
   o->slices_closed++;
@@ -300,6 +331,31 @@ double orc_vhll(double Z, double g, uint64_t S, uint64_t V, uint64_t S_Z,
                 uint64_t V_Z) {
   double n_g = orc_hll(g, S, V);
   double n_Z = orc_hll(Z, S_Z, V_Z);
+  double n = (Z * g / (Z - g)) * (n_g / g - n_Z / Z);
+  return n > 0.0 ? n : 0.0;
+}
+
+/* LogLog bias constant (Durand & Flajolet 2003):
+ *   alpha_m = (Gamma(-1/m) (1 - 2^(1/m)) / ln 2)^(-m),
+ * with 1 - 2^(1/m) = -expm1(ln 2 / m) to keep its digits for large m. */
+double orc_loglog_alpha(double m) {
+  double base = tgamma(-1.0 / m) * -expm1(log(2.0) / m) / log(2.0);
+  return pow(base, -m);
+}
+
+/* LogLog estimate of m registers whose values sum to L. */
+double orc_loglog(double m, uint64_t L) {
+  return orc_loglog_alpha(m) * m * exp2((double)L / m);
+}
+
+/* PCSA estimate of m bitmaps whose statistics sum to P (Flajolet & Martin
+ * 1985, phi = 0.77351). */
+double orc_pcsa(double m, uint64_t P) {
+  return m / 0.77351 * exp2((double)P / m);
+}
+
+/* The virtual-sharing noise removal of vHLL applied to any estimate pair. */
+static double orc_denoise(double Z, double g, double n_g, double n_Z) {
   double n = (Z * g / (Z - g)) * (n_g / g - n_Z / Z);
   return n > 0.0 ? n : 0.0;
 }
@@ -377,6 +433,30 @@ int orc_estimate(const orc_t *o, const uint32_t *aips, uint64_t n,
   return 0;
 }
 
+/* Estimates with the LogLog (which = 1) or PCSA (which = 2) statistic of
+ * the host's g virtual BDRs, FP64.  Alg. 5's getSumLBP1 is the LogLog sum.
+ * Returns -1 before the first slide, -2 for PCSA on a layout other than
+ * gsmall. */
+int orc_estimate_alt(const orc_t *o, int which, const uint32_t *aips, uint64_t n,
+                     double *out) {
+  if (o->slices_closed == 0) return -1;
+  if (which == 2 && o->variant != ORC_GSMALL) return -2;
+  const double Z = (double)o->Z;
+  const double n_Z = which == 1 ? orc_loglog(Z, o->L_Z) : orc_pcsa(Z, o->P_Z);
+  for (uint64_t h = 0; h < n; ++h) {
+    uint32_t b = orc_host_b(o, aips[h]);
+    uint32_t g = 1u << b;
+    uint64_t sum = 0;
+    for (uint32_t i = 0; i < g; ++i) {
+      uint64_t j = orc_get_phy_idx(o, aips[h], i);
+      sum += which == 1 ? o->reg[j] : o->pcsa[j];
+    }
+    double n_g = which == 1 ? orc_loglog((double)g, sum) : orc_pcsa((double)g, sum);
+    out[h] = orc_denoise(Z, (double)g, n_g, n_Z);
+  }
+  return 0;
+}
+
 /* ---------------------------------------------------------- inspection */
 
 /* Logical state: DR as [Z][R] (entries 1..R), bs [Z], reg [Z]; any output
@@ -435,6 +515,15 @@ void orc_pool_sums_get(const orc_t *o, uint64_t *S_Z, uint64_t *V_Z) {
   *S_Z = o->S_Z;
   *V_Z = o->V_Z;
 }
+
+/* Pool sums of the registers (LogLog) and PCSA statistics. */
+void orc_pool_sums_alt(const orc_t *o, uint64_t *L_Z, uint64_t *P_Z) {
+  *L_Z = o->L_Z;
+  *P_Z = o->P_Z;
+}
+
+/* PCSA statistic of every BDR at the last slide. */
+void orc_get_pcsa(const orc_t *o, uint8_t *out) { memcpy(out, o->pcsa, (size_t)o->Z); }
 
 /* Table 1: bits of one BDR per variant, with log2(n/g) read as R DRs and
  * log2(k+1) as the DR width w.  serial stores nowLBP1 in
