@@ -148,6 +148,28 @@ VBDR_API int vbdr_slide(vbdr_t h, void *stream);
 VBDR_API int vbdr_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts,
                   float *d_out, void *stream);
 
+/* Estimators the BDR pool can serve besides HyperLogLog (Sec. 4.1 notes
+ * PCSA and LogLog counting), each with the same virtual-sharing noise
+ * removal n = Z g/(Z-g) (n_g/g - n_Z/Z), clamped at 0, in FP64:
+ *   VBDR_EST_HLL   : vbdr_estimate.
+ *   VBDR_EST_LOGLOG: n_m = alpha_m m 2^(sum M / m) over the registers M
+ *                    (Alg. 5's getSumLBP1 is the sum), alpha_m =
+ *                    (Gamma(-1/m) (1 - 2^(1/m)) / ln 2)^(-m) (Durand &
+ *                    Flajolet 2003).  Any layout.
+ *   VBDR_EST_PCSA  : n_m = (m / 0.77351) 2^(sum R / m) (Flajolet & Martin
+ *                    1985), R of a BDR = the number of active DRs from
+ *                    LBP1 1 up to the first inactive one, i.e. the lowest
+ *                    unset position of the window bitmap.  Needs a bitmap of
+ *                    every LBP1 seen, which only gsmall's Alg. 9 records:
+ *                    gsmall only (its slide stores R for every BDR). */
+typedef enum { VBDR_EST_HLL = 0, VBDR_EST_LOGLOG = 1, VBDR_EST_PCSA = 2 } vbdr_estimator;
+
+/* vbdr_estimate with the estimator of the given vbdr_estimator.
+ * Errors: as vbdr_estimate; VBDR_EINVAL also for an unknown estimator or
+ * VBDR_EST_PCSA on a layout other than VBDR_GSMALL. */
+VBDR_API int vbdr_estimate_alt(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts, float *d_out,
+                               int estimator, void *stream);
+
 /* vbdr_estimate for HOST buffers: h_aips is copied in, h_out is written back
  * on the stream (valid once the stream has passed the call).  Uses a staging
  * buffer owned by the handle, grown as needed.  Errors: as vbdr_estimate,
@@ -409,6 +431,16 @@ VBDR_API int vbdr_copy_state(vbdr_t h, uint8_t *h_dr, uint32_t *h_bs, uint8_t *h
 
 /* Pool sums of the last slide (see vbdr_slide). */
 VBDR_API int vbdr_copy_pool_sums(vbdr_t h, uint64_t *S_Z, uint64_t *V_Z, void *stream);
+
+/* Pool sums of the last slide for VBDR_EST_LOGLOG and VBDR_EST_PCSA: L_Z =
+ * sum of the Z registers, P_Z = sum of the Z PCSA statistics (0 unless
+ * gsmall).  Synchronous.  Errors: VBDR_EINVAL, VBDR_ECUDA. */
+VBDR_API int vbdr_copy_pool_sums_alt(vbdr_t h, uint64_t *L_Z, uint64_t *P_Z, void *stream);
+
+/* The PCSA statistic of every physical BDR at the last slide (h_pcsa: Z
+ * bytes, host).  gsmall only.  Synchronous.  Errors: VBDR_EINVAL,
+ * VBDR_ECUDA. */
+VBDR_API int vbdr_copy_pcsa(vbdr_t h, uint8_t *h_pcsa, void *stream);
 
 /* Human-readable text of a vbdr_status. */
 VBDR_API const char *vbdr_strerror(int status);

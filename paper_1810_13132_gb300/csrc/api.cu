@@ -70,7 +70,9 @@ __global__ void init_kernel(Dims d, DevState s, uint32_t word_init, uint32_t kta
     const uint64_t s1 = vbk::mix64(i ^ K0) >> 32;
     s.ktab[i] = vbk::make_kent(vbk::mix64(s1));
   }
-  if (tid < 5) s.sums[tid] = 0ull;
+  if (tid < vbk::kSums) s.sums[tid] = 0ull;
+  if (s.pcsa)
+    for (uint64_t j = tid; j < d.Zs; j += stride) s.pcsa[j] = 0u;
 }
 
 // HyperLogLog bias constant alpha_m (Flajolet et al. 2007).
@@ -81,6 +83,16 @@ double hll_alpha(double m) {
   return 0.7213 / (1.0 + 1.079 / m);
 }
 
+// LogLog bias constant (Durand & Flajolet 2003):
+//   alpha_m = (Gamma(-1/m) (1 - 2^(1/m)) / ln 2)^(-m),
+// with 1 - 2^(1/m) taken as -expm1(ln 2 / m) so that large m keep their
+// digits.  PCSA's correction factor phi (Flajolet & Martin 1985).
+double loglog_alpha(double m) {
+  const double base = std::tgamma(-1.0 / m) * -std::expm1(std::log(2.0) / m) / std::log(2.0);
+  return std::pow(base, -m);
+}
+constexpr double kPcsaPhi = 0.77351;
+
 void fill_est_const(const Dims &d, EstConst *c) {
   const double Z = (double)d.Z;
   for (int b = 0; b <= vbk::kMaxLog2G; ++b) {
@@ -90,6 +102,13 @@ void fill_est_const(const Dims &d, EstConst *c) {
     c->lng[b] = std::log(g);
   }
   c->amm_Z = hll_alpha(Z) * Z * Z;
+  for (int b = 0; b <= vbk::kMaxLog2G; ++b) {
+    const double g = (double)(1u << b);
+    c->ll[b] = b ? loglog_alpha(g) * g : 0.0;
+    c->pc[b] = g / kPcsaPhi;
+  }
+  c->ll_Z = loglog_alpha(Z) * Z;
+  c->pc_Z = Z / kPcsaPhi;
 }
 
 int fail_cuda(vbdr *h, cudaError_t e) {
@@ -110,6 +129,7 @@ void free_state(vbdr *h) {
   cudaFree(h->s.bs);
   cudaFree(h->s.now);
   cudaFree(h->s.reg);
+  cudaFree(h->s.pcsa);
   cudaFree(h->s.ktab);
   cudaFree(h->s.lnv);
   cudaFree(h->s.sums);
@@ -200,9 +220,10 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
       std::max<uint64_t>(d.Zs, (d.Z + vbk::kPlanChunk - 1) / vbk::kPlanChunk * vbk::kPlanChunk);
   if (e == cudaSuccess) e = cudaMalloc(&h->s.reg, (size_t)reg_bytes);
   if (e == cudaSuccess) e = cudaMemset(h->s.reg, 0, (size_t)reg_bytes);
+  if (e == cudaSuccess && h->layout == VBDR_GSMALL) e = cudaMalloc(&h->s.pcsa, (size_t)d.Zs);
   if (e == cudaSuccess) e = cudaMalloc(&h->s.ktab, (size_t)kn * sizeof(vbk::KEnt));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.lnv, vbk::kLnTab * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&h->s.sums, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->s.sums, vbk::kSums * sizeof(unsigned long long));
   if (e == cudaSuccess) {
     double lnv[vbk::kLnTab];
     lnv[0] = 0.0;
@@ -337,6 +358,21 @@ int vbdr_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n, float *d_out,
                                             (cudaStream_t)stream, h->est_cfg));
 }
 
+int vbdr_estimate_alt(vbdr_t h, const uint32_t *d_aips, uint64_t n, float *d_out,
+                      int estimator, void *stream) {
+  if (!h) return VBDR_EINVAL;
+  if (estimator == VBDR_EST_HLL) return vbdr_estimate(h, d_aips, n, d_out, stream);
+  if (estimator != VBDR_EST_LOGLOG && estimator != VBDR_EST_PCSA) return VBDR_EINVAL;
+  if (estimator == VBDR_EST_PCSA && h->layout != VBDR_GSMALL) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!h->slid) return VBDR_EORDER;
+  if (n == 0) return VBDR_OK;
+  if (!d_aips || !d_out || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_out & 3u))
+    return VBDR_EINVAL;
+  return fail_cuda(h, vbk::launch_estimate_alt(h->d, h->s, h->est, d_aips, n, d_out, estimator,
+                                                (cudaStream_t)stream, h->est_cfg));
+}
+
 int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n, float *h_out,
                        void *stream) {
   if (!h) return VBDR_EINVAL;
@@ -426,7 +462,9 @@ int vbdr_load_virtual_registers(vbdr_t h, const uint32_t *d_aips, const uint64_t
   if (n_hosts && (!d_aips || !d_offsets || !d_vregs)) return VBDR_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = vbk::launch_load_virtual(h->d, h->s, d_aips, d_offsets, n_hosts, d_vregs, st);
-  if (e == cudaSuccess) e = vbk::launch_pool_sums(h->s.reg, h->d.Z, h->s.sums, st);
+  // no PCSA statistics at register level: they read as 0
+  if (e == cudaSuccess && h->s.pcsa) e = cudaMemsetAsync(h->s.pcsa, 0, h->d.Zs, st);
+  if (e == cudaSuccess) e = vbk::launch_pool_sums(h->s.reg, h->s.pcsa, h->d.Z, h->s.sums, st);
   int rc = fail_cuda(h, e);
   if (rc == VBDR_OK) h->slid = true;
   return rc;
@@ -485,20 +523,22 @@ int vbdr_autotune_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts, f
 namespace {
 // Checkpoint layout: header, then the raw device buffers in a fixed order.
 struct CkptHeader {
-  char magic[8];  // "VBDRCKP1"
+  char magic[8];  // "VBDRCKP2"
   uint32_t k, log2_g, log2_g_min, group_rule, layout, slid;
-  uint64_t num_bdr, seed, drv_bytes, slice_bytes, reg_bytes;
+  uint64_t num_bdr, seed, drv_bytes, slice_bytes, reg_bytes, pcsa_bytes;
 };
 
-void ckpt_sizes(const vbdr *h, uint64_t *drv, uint64_t *slice, uint64_t *reg) {
+void ckpt_sizes(const vbdr *h, uint64_t *drv, uint64_t *slice, uint64_t *reg, uint64_t *pcsa) {
   *drv = (uint64_t)h->d.P * h->d.Zs * 4;
   *slice = h->s.bs ? h->d.Z * 4 : (h->s.now ? h->d.Zs : 0);
   *reg = h->d.Zs;
+  *pcsa = h->s.pcsa ? h->d.Zs : 0;
 }
+constexpr uint64_t kCkptSums = vbk::kSums * sizeof(unsigned long long);
 
 void fill_header(const vbdr *h, CkptHeader *hd) {
   std::memset(hd, 0, sizeof(*hd));
-  std::memcpy(hd->magic, "VBDRCKP1", 8);
+  std::memcpy(hd->magic, "VBDRCKP2", 8);
   hd->k = h->d.k;
   hd->log2_g = h->d.b;
   hd->log2_g_min = h->d.b_min;
@@ -507,15 +547,15 @@ void fill_header(const vbdr *h, CkptHeader *hd) {
   hd->slid = h->slid ? 1u : 0u;
   hd->num_bdr = h->d.Z;
   hd->seed = h->d.A0;
-  ckpt_sizes(h, &hd->drv_bytes, &hd->slice_bytes, &hd->reg_bytes);
+  ckpt_sizes(h, &hd->drv_bytes, &hd->slice_bytes, &hd->reg_bytes, &hd->pcsa_bytes);
 }
 }  // namespace
 
 int vbdr_state_bytes(vbdr_t h, uint64_t *bytes) {
   if (!h || !bytes) return VBDR_EINVAL;
-  uint64_t a, b, c;
-  ckpt_sizes(h, &a, &b, &c);
-  *bytes = sizeof(CkptHeader) + a + b + c + 2 * sizeof(unsigned long long);
+  uint64_t a, b, c, q;
+  ckpt_sizes(h, &a, &b, &c, &q);
+  *bytes = sizeof(CkptHeader) + a + b + c + q + kCkptSums;
   return VBDR_OK;
 }
 
@@ -540,8 +580,10 @@ int vbdr_save(vbdr_t h, void *h_buf, uint64_t cap, void *stream) {
   p += hd.slice_bytes;
   if (e == cudaSuccess) e = cudaMemcpy(p, h->s.reg, hd.reg_bytes, cudaMemcpyDeviceToHost);
   p += hd.reg_bytes;
-  if (e == cudaSuccess) e = cudaMemcpy(p, h->s.sums, 2 * sizeof(unsigned long long),
-                                       cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && hd.pcsa_bytes)
+    e = cudaMemcpy(p, h->s.pcsa, hd.pcsa_bytes, cudaMemcpyDeviceToHost);
+  p += hd.pcsa_bytes;
+  if (e == cudaSuccess) e = cudaMemcpy(p, h->s.sums, kCkptSums, cudaMemcpyDeviceToHost);
   return fail_cuda(h, e);
 }
 
@@ -566,8 +608,10 @@ int vbdr_load(vbdr_t h, const void *h_buf, uint64_t len, void *stream) {
   p += hd.slice_bytes;
   if (e == cudaSuccess) e = cudaMemcpy(h->s.reg, p, hd.reg_bytes, cudaMemcpyHostToDevice);
   p += hd.reg_bytes;
-  if (e == cudaSuccess)
-    e = cudaMemcpy(h->s.sums, p, 2 * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && hd.pcsa_bytes)
+    e = cudaMemcpy(h->s.pcsa, p, hd.pcsa_bytes, cudaMemcpyHostToDevice);
+  p += hd.pcsa_bytes;
+  if (e == cudaSuccess) e = cudaMemcpy(h->s.sums, p, kCkptSums, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) h->slid = hd.slid != 0;
   return fail_cuda(h, e);
 }
@@ -626,6 +670,29 @@ int vbdr_copy_pool_sums(vbdr_t h, uint64_t *S_Z, uint64_t *V_Z, void *stream) {
   *S_Z = v[0];
   *V_Z = v[1];
   return VBDR_OK;
+}
+
+int vbdr_copy_pool_sums_alt(vbdr_t h, uint64_t *L_Z, uint64_t *P_Z, void *stream) {
+  if (!h || !L_Z || !P_Z) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  unsigned long long v[vbk::kSums];
+  cudaError_t e = cudaMemcpyAsync(v, h->s.sums, sizeof(v), cudaMemcpyDeviceToHost,
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fail_cuda(h, e);
+  *L_Z = v[vbk::kSumL];
+  *P_Z = v[vbk::kSumP];
+  return VBDR_OK;
+}
+
+int vbdr_copy_pcsa(vbdr_t h, uint8_t *h_pcsa, void *stream) {
+  if (!h || !h_pcsa) return VBDR_EINVAL;
+  if (h->layout != VBDR_GSMALL) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  cudaError_t e = cudaMemcpyAsync(h_pcsa, h->s.pcsa, h->d.Z, cudaMemcpyDeviceToHost,
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  return fail_cuda(h, e);
 }
 
 /* ---------------------------------------------------------------- plans */

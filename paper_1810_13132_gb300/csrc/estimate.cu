@@ -32,7 +32,10 @@ constexpr int kMaxEstWarps = 16;  // blocks of up to 512 threads
 constexpr int kGatherUnroll = 8;
 // What the kernel produces per host: the estimate, or also the learned
 // correction's feature row.
-enum EstMode { kPlain = 0, kFeatures = 1 };
+// kLogLog / kPcsa: the same walk over the host's virtual BDRs summing the
+// register (Alg. 5's getSumLBP1, the LogLog statistic) or the PCSA statistic
+// of each BDR, finished with that estimator and the same noise removal.
+enum EstMode { kPlain = 0, kFeatures = 1, kLogLog = 2, kPcsa = 3 };
 
 // A warp owns a batch of 32 hosts and splits its lanes into 32/T groups of
 // T lanes; in T steps each group gathers one host of the batch.  The host
@@ -53,6 +56,8 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
   constexpr uint32_t G = 32 / T;  // hosts gathered at once per warp
   constexpr int WARPS = kMaxEstWarps;
   constexpr bool HIST = MODE == kFeatures;
+  constexpr bool SUM = MODE == kLogLog || MODE == kPcsa;  // plain sum of the values
+  const uint8_t *vals = MODE == kPcsa ? s.pcsa : s.reg;
   __shared__ KEnt kt_s[SMEM_KT ? kKtabSize : 1];
   __shared__ double lnv_s[kLnTab];
   __shared__ double nZZ_s;
@@ -64,7 +69,15 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
     for (uint32_t i = threadIdx.x; i < gmax; i += blockDim.x) kt_s[i] = s.ktab[i];
   }
   for (uint32_t i = threadIdx.x; i < (uint32_t)kLnTab; i += blockDim.x) lnv_s[i] = s.lnv[i];
-  if (threadIdx.x == 0) nZZ_s = pool_noise(d, s, c);
+  if (threadIdx.x == 0) {
+    // pool estimate per register, n_Z / Z
+    if constexpr (MODE == kLogLog)
+      nZZ_s = c.ll_Z * exp2((double)s.sums[kSumL] / (double)d.Z) / (double)d.Z;
+    else if constexpr (MODE == kPcsa)
+      nZZ_s = c.pc_Z * exp2((double)s.sums[kSumP] / (double)d.Z) / (double)d.Z;
+    else
+      nZZ_s = pool_noise(d, s, c);
+  }
   __syncthreads();
   const KEnt *kt = SMEM_KT ? kt_s : s.ktab;
   const double nZZ = nZZ_s;
@@ -98,7 +111,7 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
           M[u] = 0xffu;
           if (i < g) {
             const uint32_t pidx = reduce32(hash32(aip, kt[i]), d.zmul);
-            M[u] = __ldg(s.reg + pidx);
+            M[u] = __ldg(vals + pidx);
           }
         }
 #pragma unroll
@@ -106,6 +119,8 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
           if (M[u] != 0xffu) {
             if constexpr (HIST) {
               atomicAdd(&hrow[wib][lane][M[u] >> 2], 1u << (8u * (M[u] & 3u)));
+            } else if constexpr (SUM) {
+              S += M[u];
             } else {
               S += 1ull << (32u - M[u]);
               V += (M[u] == 0u);
@@ -164,9 +179,17 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
       const unsigned long long myS = resS[wib][lane];
       const uint32_t myV = resV[wib][lane];
       const uint32_t b = host_b(d, aip_l);
-      double n_g;
-      const double est = host_estimate(myS, myV, b, c, lnv_s, nZZ, &n_g);
-      if constexpr (MODE == kPlain) {
+      double n_g = 0.0, est;
+      if constexpr (SUM) {
+        // n_g = const_g 2^(sum / g); n = Z g / (Z - g) (n_g / g - n_Z / Z)
+        const double base = MODE == kLogLog ? c.ll[b] : c.pc[b];
+        n_g = base * exp2(ldexp((double)myS, -(int)b));
+        est = c.kz[b] * (ldexp(n_g, -(int)b) - nZZ);
+        if (!(est > 0.0)) est = 0.0;
+      } else {
+        est = host_estimate(myS, myV, b, c, lnv_s, nZZ, &n_g);
+      }
+      if constexpr (MODE != kFeatures) {
         out[h_l] = (float)est;
       } else {
         __align__(16) __nv_bfloat16 x[16];
@@ -231,6 +254,14 @@ cudaError_t launch_estimate(const Dims &d, const DevState &s, const EstConst &c,
                             const uint32_t *aips, uint64_t n, float *out,
                             cudaStream_t st, EstLaunch cfg) {
   return launch_mode<kPlain>(d, s, c, aips, n, out, st, cfg, nullptr);
+}
+
+cudaError_t launch_estimate_alt(const Dims &d, const DevState &s, const EstConst &c,
+                                const uint32_t *aips, uint64_t n, float *out, int which,
+                                cudaStream_t st, EstLaunch cfg) {
+  if (which == 1) return launch_mode<kLogLog>(d, s, c, aips, n, out, st, cfg, nullptr);
+  if (which == 2) return launch_mode<kPcsa>(d, s, c, aips, n, out, st, cfg, nullptr);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_features(const Dims &d, const DevState &s, const EstConst &c,

@@ -5,7 +5,8 @@
 // (host aip's virtual index i -> BDR H(aip, Z, s1(i))); BDRs that no virtual
 // register maps to hold 0.  This is how a workload too large to scan (4M
 // hosts with cardinalities up to 1e7) is put under the estimator.
-// launch_pool_sums: S_Z = sum_j 2^(32 - reg_j), V_Z = #{reg_j = 0}.
+// launch_pool_sums: S_Z = sum_j 2^(32 - reg_j), V_Z = #{reg_j = 0}, L_Z =
+// sum_j reg_j and P_Z = sum_j pcsa_j (0 without a PCSA array).
 #include "vbdr_internal.cuh"
 
 namespace vbk {
@@ -47,33 +48,48 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 __global__ void __launch_bounds__(kThreads)
-    pool_sums_kernel(const uint8_t *__restrict__ reg, uint64_t Z, unsigned long long *sums) {
-  unsigned long long S = 0, V = 0;
+    pool_sums_kernel(const uint8_t *__restrict__ reg, const uint8_t *__restrict__ pcsa, uint64_t Z,
+                     unsigned long long *sums) {
+  unsigned long long S = 0, V = 0, L = 0, Pc = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < Z; j += stride) {
     const uint32_t M = reg[j];
     S += 1ull << (32u - M);
     V += (M == 0u);
+    L += M;
+    if (pcsa) Pc += pcsa[j];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     S += __shfl_down_sync(0xffffffffu, S, o);
     V += __shfl_down_sync(0xffffffffu, V, o);
+    L += __shfl_down_sync(0xffffffffu, L, o);
+    Pc += __shfl_down_sync(0xffffffffu, Pc, o);
   }
-  __shared__ unsigned long long sS[kThreads / 32], sV[kThreads / 32];
+  __shared__ unsigned long long sS[kThreads / 32], sV[kThreads / 32], sL[kThreads / 32],
+      sP[kThreads / 32];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  if (lane == 0) { sS[warp] = S; sV[warp] = V; }
+  if (lane == 0) { sS[warp] = S; sV[warp] = V; sL[warp] = L; sP[warp] = Pc; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (uint32_t i = 1; i < blockDim.x / 32; ++i) { S += sS[i]; V += sV[i]; }
-    atomicAdd(&sums[3], S);
-    atomicAdd(&sums[4], V);
+    for (uint32_t i = 1; i < blockDim.x / 32; ++i) {
+      S += sS[i];
+      V += sV[i];
+      L += sL[i];
+      Pc += sP[i];
+    }
+    atomicAdd(&sums[kSumSPart], S);
+    atomicAdd(&sums[kSumVPart], V);
+    atomicAdd(&sums[kSumLPart], L);
+    atomicAdd(&sums[kSumPPart], Pc);
     __threadfence();
-    if (atomicAdd(&sums[2], 1ull) == gridDim.x - 1) {
+    if (atomicAdd(&sums[kSumCounter], 1ull) == gridDim.x - 1) {
       __threadfence();
-      sums[0] = atomicExch(&sums[3], 0ull);
-      sums[1] = atomicExch(&sums[4], 0ull);
-      sums[2] = 0ull;
+      sums[kSumS] = atomicExch(&sums[kSumSPart], 0ull);
+      sums[kSumV] = atomicExch(&sums[kSumVPart], 0ull);
+      sums[kSumL] = atomicExch(&sums[kSumLPart], 0ull);
+      sums[kSumP] = atomicExch(&sums[kSumPPart], 0ull);
+      sums[kSumCounter] = 0ull;
     }
   }
 }
@@ -99,9 +115,9 @@ cudaError_t launch_load_virtual(const Dims &d, const DevState &s, const uint32_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_pool_sums(const uint8_t *reg, uint64_t Z, unsigned long long *sums,
-                             cudaStream_t st) {
-  pool_sums_kernel<<<grid_for(Z, 8), kThreads, 0, st>>>(reg, Z, sums);
+cudaError_t launch_pool_sums(const uint8_t *reg, const uint8_t *pcsa, uint64_t Z,
+                             unsigned long long *sums, cudaStream_t st) {
+  pool_sums_kernel<<<grid_for(Z, 8), kThreads, 0, st>>>(reg, pcsa, Z, sums);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@
 // join while admitted ones keep running, continuous-batching style.
 // Waiting is host-side only (condition variable, event polling with a
 // deadline); no kernel here waits on anything.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -127,8 +128,11 @@ uint64_t vbdr_server_tenant_bytes(const vbdr_config *cfg, uint64_t max_pairs, ui
   const uint32_t b_min = cfg->log2_g_min ? cfg->log2_g_min : cfg->log2_g;
   const uint32_t R = 32 - b_min, F = 32 / w, P = (R + F - 1) / F;
   const uint64_t Zs = (cfg->num_bdr + 3) & ~3ull;
-  uint64_t bytes = Zs * (4ull * P + 1) + (cfg->layout == VBDR_GFAST ? 4 * cfg->num_bdr : 0) +
-                   (cfg->layout == VBDR_SERIAL ? Zs : 0);
+  const uint64_t chunk = 1ull << 15;  // registers are allocated in whole 32 KiB chunks
+  const uint64_t reg = std::max<uint64_t>(Zs, (cfg->num_bdr + chunk - 1) / chunk * chunk);
+  uint64_t bytes = Zs * 4ull * P + reg + (cfg->layout == VBDR_GFAST ? 4 * cfg->num_bdr : 0) +
+                   (cfg->layout == VBDR_SERIAL ? Zs : 0) +
+                   (cfg->layout == VBDR_GSMALL ? Zs : 0);  // PCSA statistics
   bytes += 64ull << 10;                                // tables, sums
   bytes += 2 * (max_pairs * 8 + 8 + n_hosts * 4);      // staging slots
   bytes += n_hosts * 4;                                // host list

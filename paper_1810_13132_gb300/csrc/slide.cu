@@ -106,9 +106,32 @@ __device__ __forceinline__ void set_dr_of_top_bit(uint32_t (&w)[PMAX], uint32_t 
   }
 }
 
+// PCSA statistic of one BDR (gsmall: DR[r] active iff LBP1 r was seen in the
+// window, a bitmap): the number of active DRs from LBP1 1 up to the first
+// inactive one, i.e. the index of the bitmap's lowest unset position.
+// Fields past R are never active, so the count stops at R.
+template <int W, int P>
+__device__ __forceinline__ uint32_t pcsa_of(const uint32_t (&w)[P], uint32_t krep_even) {
+  uint32_t n = 0;
+  bool run = true;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const uint32_t inactive = ~active_fields<W>(w[p], krep_even) & Fields<W>::LSB;
+    if (run) {
+      if (inactive) {
+        n += (uint32_t)(__ffs(inactive) - 1) / W;
+        run = false;
+      } else {
+        n += Fields<W>::F;
+      }
+    }
+  }
+  return n;
+}
+
 template <int W, int P, bool GFAST>
 __device__ __forceinline__ uint32_t slide_one(uint32_t (&w)[P], uint32_t bsv,
-                                              uint32_t krep_even) {
+                                              uint32_t krep_even, uint32_t *pcsa) {
   if constexpr (GFAST) {
 #pragma unroll
     for (int p = 0; p < P; ++p) w[p] = sat_inc<W>(w[p]);
@@ -116,6 +139,7 @@ __device__ __forceinline__ uint32_t slide_one(uint32_t (&w)[P], uint32_t bsv,
     return register_of<W, P>(w, krep_even);
   } else {
     const uint32_t reg = register_of<W, P>(w, krep_even);
+    *pcsa = pcsa_of<W, P>(w, krep_even);
 #pragma unroll
     for (int p = 0; p < P; ++p) w[p] = sat_inc<W>(w[p]);
     return reg;
@@ -134,7 +158,7 @@ template <int W, int P, int LAY>
 __global__ void __launch_bounds__(kSlideThreads)
     slide_kernel(Dims d, DevState s, uint32_t krep_even) {
   constexpr bool GFAST = LAY != kLayoutGsmall;  // fold a slice maximum (Alg. 1 / 6)
-  unsigned long long S = 0, V = 0;
+  unsigned long long S = 0, V = 0, L = 0, Pc = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t quads = d.Z >> 2;
@@ -157,18 +181,22 @@ __global__ void __launch_bounds__(kSlideThreads)
         set_comp(bsq, c, nv ? 1u << (nv - 1u) : 0u);
       }
     }
-    uint32_t regs = 0;
+    uint32_t regs = 0, pcs = 0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       uint32_t w[P];
 #pragma unroll
       for (int p = 0; p < P; ++p) w[p] = comp(v[p], c);
-      const uint32_t reg = slide_one<W, P, GFAST>(w, comp(bsq, c), krep_even);
+      uint32_t pc = 0;
+      const uint32_t reg = slide_one<W, P, GFAST>(w, comp(bsq, c), krep_even, &pc);
 #pragma unroll
       for (int p = 0; p < P; ++p) set_comp(v[p], c, w[p]);
       regs |= reg << (8 * c);
+      pcs |= pc << (8 * c);
       S += 1ull << (32u - reg);
       V += (reg == 0u);
+      L += reg;
+      Pc += pc;
     }
 #pragma unroll
     for (int p = 0; p < P; ++p)
@@ -181,6 +209,7 @@ __global__ void __launch_bounds__(kSlideThreads)
       if (bsq.x | bsq.y | bsq.z | bsq.w) __stcs(reinterpret_cast<uint32_t *>(s.now + j), 0u);
     }
     __stcs(reinterpret_cast<uint32_t *>(s.reg + j), regs);
+    if constexpr (LAY == kLayoutGsmall) __stcs(reinterpret_cast<uint32_t *>(s.pcsa + j), pcs);
   }
   // the last Z mod 4 BDRs, one thread each
   if (tid < (d.Z & 3u)) {
@@ -191,38 +220,54 @@ __global__ void __launch_bounds__(kSlideThreads)
     uint32_t bsv = 0u;
     if constexpr (LAY == kLayoutGfast) bsv = s.bs[j];
     if constexpr (LAY == kLayoutSerial) bsv = s.now[j] ? 1u << (s.now[j] - 1u) : 0u;
-    const uint32_t reg = slide_one<W, P, GFAST>(w, bsv, krep_even);
+    uint32_t pc = 0;
+    const uint32_t reg = slide_one<W, P, GFAST>(w, bsv, krep_even, &pc);
 #pragma unroll
     for (int p = 0; p < P; ++p) s.drv[(uint64_t)p * d.Zs + j] = w[p];
     if (LAY == kLayoutGfast && bsv) s.bs[j] = 0u;
     if (LAY == kLayoutSerial && bsv) s.now[j] = 0u;
     s.reg[j] = (uint8_t)reg;
+    if (LAY == kLayoutGsmall) s.pcsa[j] = (uint8_t)pc;
     S += 1ull << (32u - reg);
     V += (reg == 0u);
+    L += reg;
+    Pc += pc;
   }
   // block reduction of the pool sums
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     S += __shfl_down_sync(0xffffffffu, S, o);
     V += __shfl_down_sync(0xffffffffu, V, o);
+    L += __shfl_down_sync(0xffffffffu, L, o);
+    Pc += __shfl_down_sync(0xffffffffu, Pc, o);
   }
-  __shared__ unsigned long long sS[kSlideThreads / 32], sV[kSlideThreads / 32];
+  __shared__ unsigned long long sS[kSlideThreads / 32], sV[kSlideThreads / 32],
+      sL[kSlideThreads / 32], sP[kSlideThreads / 32];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  if (lane == 0) { sS[warp] = S; sV[warp] = V; }
+  if (lane == 0) { sS[warp] = S; sV[warp] = V; sL[warp] = L; sP[warp] = Pc; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (uint32_t i = 1; i < blockDim.x / 32; ++i) { S += sS[i]; V += sV[i]; }
-    atomicAdd(&s.sums[3], S);
-    atomicAdd(&s.sums[4], V);
+    for (uint32_t i = 1; i < blockDim.x / 32; ++i) {
+      S += sS[i];
+      V += sV[i];
+      L += sL[i];
+      Pc += sP[i];
+    }
+    atomicAdd(&s.sums[kSumSPart], S);
+    atomicAdd(&s.sums[kSumVPart], V);
+    atomicAdd(&s.sums[kSumLPart], L);
+    atomicAdd(&s.sums[kSumPPart], Pc);
     __threadfence();
     // The last block to finish publishes the totals and resets the partials
     // for the next slide (the counter pattern keeps the slide one launch).
-    const unsigned long long done = atomicAdd(&s.sums[2], 1ull);
+    const unsigned long long done = atomicAdd(&s.sums[kSumCounter], 1ull);
     if (done == gridDim.x - 1) {
       __threadfence();
-      s.sums[0] = atomicExch(&s.sums[3], 0ull);
-      s.sums[1] = atomicExch(&s.sums[4], 0ull);
-      s.sums[2] = 0ull;
+      s.sums[kSumS] = atomicExch(&s.sums[kSumSPart], 0ull);
+      s.sums[kSumV] = atomicExch(&s.sums[kSumVPart], 0ull);
+      s.sums[kSumL] = atomicExch(&s.sums[kSumLPart], 0ull);
+      s.sums[kSumP] = atomicExch(&s.sums[kSumPPart], 0ull);
+      s.sums[kSumCounter] = 0ull;
     }
   }
 }

@@ -103,11 +103,18 @@ struct Dims {
 // computed on the host with the same IEEE operations, in the same order, as
 // the plain formula): amm[b] = alpha_g * g * g, kz[b] = Z * g / (Z - g),
 // lng[b] = ln g; amm_Z = alpha_Z * Z * Z for the pool.
+// LogLog and PCSA (the BDR pool serves both, Sec. 4.1): ll[b] = alpha^LL_g g
+// with alpha^LL_m = (Gamma(-1/m) (1 - 2^(1/m)) / ln 2)^(-m) (Durand &
+// Flajolet 2003), pc[b] = g / 0.77351 (Flajolet & Martin 1985); ll_Z, pc_Z
+// the same for the pool.
 struct EstConst {
   double amm[kMaxLog2G + 1];
   double kz[kMaxLog2G + 1];
   double lng[kMaxLog2G + 1];
   double amm_Z;
+  double ll[kMaxLog2G + 1];
+  double pc[kMaxLog2G + 1];
+  double ll_Z, pc_Z;
 };
 
 struct DevState {
@@ -115,10 +122,19 @@ struct DevState {
   uint32_t *bs;      // [Z] (gfast only, else nullptr)
   uint8_t *now;      // [Zs] nowLBP1 (serial only, else nullptr)
   uint8_t *reg;      // [Z]
+  uint8_t *pcsa;     // [Zs] gsmall only: PCSA statistic of the closed window
   KEnt *ktab;        // [max(g_max, kKtabSize)]
   double *lnv;       // [kLnTab] ln(v)
-  unsigned long long *sums;  // [0] S_Z, [1] V_Z, [2] slide block counter,
-                             // [3] S partial, [4] V partial
+  unsigned long long *sums;  // [kSums]: pool sums of the last slide and the
+                             // partials of their reduction (kSum* below)
+};
+
+// Slots of DevState::sums.  Totals: S_Z = sum 2^(32 - reg), V_Z = #{reg = 0},
+// L_Z = sum reg (LogLog), P_Z = sum pcsa (PCSA); each has a partial that the
+// reducing launch accumulates and its last block moves into the total.
+enum : int {
+  kSumS = 0, kSumV = 1, kSumCounter = 2, kSumSPart = 3, kSumVPart = 4,
+  kSumL = 5, kSumLPart = 6, kSumP = 7, kSumPPart = 8, kSums = 16
 };
 
 // host b of aip (group_rule 1: four groups by the top two address bits)
@@ -185,8 +201,11 @@ float mlp_nmax(const vbdr_mlp *m);
 cudaError_t launch_load_virtual(const Dims &d, const DevState &s, const uint32_t *aips,
                                 const uint64_t *offsets, uint64_t n, const uint8_t *vregs,
                                 cudaStream_t st);
-cudaError_t launch_pool_sums(const uint8_t *reg, uint64_t Z, unsigned long long *sums,
-                             cudaStream_t st);
+cudaError_t launch_pool_sums(const uint8_t *reg, const uint8_t *pcsa, uint64_t Z,
+                             unsigned long long *sums, cudaStream_t st);
+cudaError_t launch_estimate_alt(const Dims &d, const DevState &s, const EstConst &c,
+                                const uint32_t *aips, uint64_t n, float *out, int which,
+                                cudaStream_t st, EstLaunch cfg);
 
 // ----- estimate plans (plan.cu) -----
 // Register chunk of the planned estimate: 2^15 BDRs (32 KiB of reg); the

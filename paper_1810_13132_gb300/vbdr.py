@@ -45,6 +45,10 @@ _SIGS = {
     "vbdr_slide": (ctypes.c_int, [_VP, _VP]),
     "vbdr_estimate": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
     "vbdr_estimate_host": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
+    "vbdr_estimate_alt": (ctypes.c_int, [_VP, _VP, _U64, _VP, ctypes.c_int, _VP]),
+    "vbdr_copy_pool_sums_alt": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64),
+                                               _VP]),
+    "vbdr_copy_pcsa": (ctypes.c_int, [_VP, _VP, _VP]),
     "vbdr_plan_create": (ctypes.c_int, [_VP, _VP, _U64, ctypes.POINTER(_VP), _VP]),
     "vbdr_plan_destroy": (ctypes.c_int, [_VP]),
     "vbdr_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64),
@@ -138,6 +142,9 @@ def _stream_ptr(stream=None) -> int:
     return int(s.cuda_stream)
 
 
+ESTIMATORS = {"hll": 0, "loglog": 1, "pcsa": 2}
+
+
 @dataclass
 class Config:
     k: int
@@ -206,15 +213,22 @@ class Vbdr:
     def slide(self, stream=None) -> None:
         _check("vbdr_slide", self._L.vbdr_slide(self._h, _stream_ptr(stream)))
 
-    def estimate(self, aips, out=None, stream=None):
+    def estimate(self, aips, out=None, stream=None, estimator: str = "hll"):
+        """Estimates of aips; estimator "hll" (vHLL), "loglog" or "pcsa"
+        (gsmall only), see include/vbdr.h."""
         import torch
         assert aips.is_cuda and aips.is_contiguous()
         n = aips.numel()
         if out is None:
             out = torch.empty(n, dtype=torch.float32, device=aips.device)
-        _check("vbdr_estimate", self._L.vbdr_estimate(
-            self._h, aips.data_ptr() if n else None, n, out.data_ptr() if n else None,
-            _stream_ptr(stream)))
+        if estimator == "hll":
+            _check("vbdr_estimate", self._L.vbdr_estimate(
+                self._h, aips.data_ptr() if n else None, n, out.data_ptr() if n else None,
+                _stream_ptr(stream)))
+        else:
+            _check("vbdr_estimate_alt", self._L.vbdr_estimate_alt(
+                self._h, aips.data_ptr() if n else None, n, out.data_ptr() if n else None,
+                ESTIMATORS[estimator], _stream_ptr(stream)))
         return out
 
     def estimate_host(self, aips, out, stream=None) -> None:
@@ -325,6 +339,20 @@ class Vbdr:
         _check("vbdr_copy_pool_sums", self._L.vbdr_copy_pool_sums(
             self._h, ctypes.byref(S), ctypes.byref(V), _stream_ptr(stream)))
         return S.value, V.value
+
+    def pool_sums_alt(self, stream=None) -> tuple[int, int]:
+        """(sum of registers, sum of PCSA statistics) of the last slide."""
+        L, P = ctypes.c_uint64(), ctypes.c_uint64()
+        _check("vbdr_copy_pool_sums_alt", self._L.vbdr_copy_pool_sums_alt(
+            self._h, ctypes.byref(L), ctypes.byref(P), _stream_ptr(stream)))
+        return L.value, P.value
+
+    def pcsa_statistics(self, stream=None) -> np.ndarray:
+        """PCSA statistic of every physical BDR at the last slide (gsmall)."""
+        out = np.empty(self.cfg.num_bdr, dtype=np.uint8)
+        _check("vbdr_copy_pcsa", self._L.vbdr_copy_pcsa(self._h, out.ctypes.data,
+                                                        _stream_ptr(stream)))
+        return out
 
 
 class Plan:
