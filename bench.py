@@ -310,6 +310,10 @@ def run_ours(a):
         def est_fn(sample):
             return v.estimate(torch.from_numpy(sample.view(np.int32)).cuda()).cpu().numpy()
         mre = {"plain": _exact_mre(gen, slices, est_fn)}
+        # the other estimators the BDR pool serves (PCSA needs gsmall's bitmaps)
+        for alt in ("loglog", "pcsa") if a.layout == "gsmall" else ("loglog",):
+            mre[alt] = _exact_mre(gen, slices, lambda sample, alt=alt: v.estimate(
+                torch.from_numpy(sample.view(np.int32)).cuda(), estimator=alt).cpu().numpy())
         if mlp is not None:
             def est_fn_l(sample):
                 return v.estimate_learned(mlp, torch.from_numpy(sample.view(np.int32)).cuda()).cpu().numpy()
