@@ -115,6 +115,10 @@ VBDR_API int vbdr_scan_slice(vbdr_t h, const uint32_t *d_pairs, uint64_t n,
  * h_pairs should be pinned (cudaHostAlloc / cudaHostRegister) for full copy
  * speed; pageable memory works but is slower.  The call returns once every
  * chunk is enqueued; h_pairs must stay valid until the stream has passed it.
+ * The copies (on the handle's own copy stream) do not wait for work enqueued
+ * earlier on the stream, only the scans do: h_pairs must already hold the
+ * pairs when the call is made, and the copies overlap earlier slides and
+ * estimates on the stream.
  * Errors: as vbdr_scan_slice, plus VBDR_ENOMEM. */
 VBDR_API int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n,
                          void *stream);

@@ -310,12 +310,10 @@ int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n, void *st
       if (e != cudaSuccess) return fail_cuda(h, e);
     }
   }
-  // The copy stream must not start before earlier work on the caller's
-  // stream that this call depends on: chain it once at the start.
-  cudaEvent_t start_ev = h->ev_copied[0];
-  e = cudaEventRecord(start_ev, st);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, start_ev, 0);
-  if (e != cudaSuccess) return fail_cuda(h, e);
+  // The copies wait only for their staging buffer (ev_free), not for earlier
+  // work on the caller's stream: a slice's pairs cross to the device while
+  // the previous slice's slide and estimate still run.  The scans themselves
+  // are ordered on the stream.
   uint64_t done = 0;
   int buf = 0;
   while (done < n) {
