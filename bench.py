@@ -368,7 +368,7 @@ def run_ours(a):
     Z, P = wl["Z"], v.words
     scan_bytes = 8 * N
     slide_bytes = {"gfast": Z * ((4 * P + 4) + (4 * P + 4 + 1)),   # DRV + bsLBP1 in, DRV + bsLBP1 + reg out
-                   "gsmall": Z * (4 * P + 4 * P + 1),               # DRV in, DRV + reg out
+                   "gsmall": Z * (4 * P + 4 * P + 1 + 1),           # DRV in, DRV + reg + PCSA out
                    "serial": Z * ((4 * P + 1) + (4 * P + 1 + 1))}[a.layout]  # DRV + nowLBP1
     est_bytes = H * (4 + 4) + Z
     if planned:  # the plan is read once per launch: host list, group offsets, entries
