@@ -64,6 +64,11 @@ struct vbdr_server {
   int device = 0;
   std::mutex mu;
   std::condition_variable cv;
+  // Serialises tenant set-up (state creation, eager launches, graph capture)
+  // and tear-down across threads: device-wide calls such as
+  // cudaDeviceSynchronize or cudaFree must not run while another thread
+  // captures a graph.
+  std::mutex setup_mu;
   uint64_t in_use = 0;
   std::vector<Tenant> tenants;
 };
@@ -183,6 +188,7 @@ int vbdr_server_open(vbdr_server_t s, const vbdr_config *cfg, uint64_t max_pairs
     s->in_use += need;
   }
   cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> setup(s->setup_mu);
   Tenant &t = s->tenants[id];
   t.max_pairs = max_pairs;
   t.n_hosts = n_hosts;
@@ -223,6 +229,7 @@ int vbdr_server_open(vbdr_server_t s, const vbdr_config *cfg, uint64_t max_pairs
   if (rc == VBDR_OK) rc = capture_slot(t, t.slot[1], mlp);
   if (rc != VBDR_OK) {
     free_tenant(t);
+    setup.unlock();
     std::lock_guard<std::mutex> lock(s->mu);
     s->in_use -= need;
     s->cv.notify_all();
@@ -236,7 +243,10 @@ int vbdr_server_close(vbdr_server_t s, uint32_t tenant) {
   if (!s || tenant >= s->tenants.size() || !s->tenants[tenant].used) return VBDR_EINVAL;
   Tenant &t = s->tenants[tenant];
   const uint64_t bytes = t.bytes;
-  free_tenant(t);
+  {
+    std::lock_guard<std::mutex> setup(s->setup_mu);
+    free_tenant(t);
+  }
   std::lock_guard<std::mutex> lock(s->mu);
   s->in_use -= bytes;
   s->cv.notify_all();
