@@ -148,11 +148,10 @@ def _make_inputs(wl, seed, n_slices):
     return gen, slices
 
 
-def _exact_mre(gen, slices, est_fn, n_sample=20000, seed=3):
-    """MRE against the exact distinct counts (Definition 1) of a host sample:
-    the top 1000 hosts plus uniformly drawn others.  After at least
-    N_DISTINCT_SLICES <= k slices the window holds exactly the union of the
-    distinct slices."""
+def _exact_truth(gen, slices, n_sample=20000, seed=3):
+    """A host sample (the top 1000 hosts plus uniformly drawn others) and its
+    exact distinct counts (Definition 1).  After at least N_DISTINCT_SLICES
+    <= k slices the window holds exactly the union of the distinct slices."""
     rng = np.random.default_rng(seed)
     H = gen.aips.size
     idx = np.unique(np.concatenate([np.arange(min(1000, H)),
@@ -171,6 +170,11 @@ def _exact_mre(gen, slices, est_fn, n_sample=20000, seed=3):
     pos = np.searchsorted(hosts, sample)
     ok = (pos < hosts.size) & (hosts[np.minimum(pos, hosts.size - 1)] == sample)
     truth[ok] = cnt[pos[ok]]
+    return sample, truth
+
+
+def _exact_mre(sample, truth, est_fn):
+    """MRE and tail errors of est_fn(sample) against the exact counts."""
     est = est_fn(sample)
     live = truth > 0
     rel = np.abs(est[live] - truth[live]) / truth[live]
@@ -309,15 +313,16 @@ def run_ours(a):
     if not a.no_mre and rank == 0 and a.warmup + a.steps >= nsl and nsl <= wl["k"]:
         def est_fn(sample):
             return v.estimate(torch.from_numpy(sample.view(np.int32)).cuda()).cpu().numpy()
-        mre = {"plain": _exact_mre(gen, slices, est_fn)}
+        sample, truth = _exact_truth(gen, slices)
+        mre = {"plain": _exact_mre(sample, truth, est_fn)}
         # the other estimators the BDR pool serves (PCSA needs gsmall's bitmaps)
         for alt in ("loglog", "pcsa") if a.layout == "gsmall" else ("loglog",):
-            mre[alt] = _exact_mre(gen, slices, lambda sample, alt=alt: v.estimate(
+            mre[alt] = _exact_mre(sample, truth, lambda sample, alt=alt: v.estimate(
                 torch.from_numpy(sample.view(np.int32)).cuda(), estimator=alt).cpu().numpy())
         if mlp is not None:
             def est_fn_l(sample):
                 return v.estimate_learned(mlp, torch.from_numpy(sample.view(np.int32)).cuda()).cpu().numpy()
-            mre["learned"] = _exact_mre(gen, slices, est_fn_l)
+            mre["learned"] = _exact_mre(sample, truth, est_fn_l)
 
     # end to end through the host-buffer entry points
     e2e = None
