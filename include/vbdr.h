@@ -447,6 +447,18 @@ VBDR_API int vbdr_copy_pool_sums_alt(vbdr_t h, uint64_t *L_Z, uint64_t *P_Z, voi
 VBDR_API int vbdr_copy_pcsa(vbdr_t h, uint8_t *h_pcsa, void *stream);
 
 /* Human-readable text of a vbdr_status. */
+/* Failure detection of the device-side waits.  The planned estimate and the
+ * MLP kernels wait on mbarriers with a bounded wait (0.2 s): a wait that
+ * expires sets the kernel's error word (vbdr_plan_status reports
+ * VBDR_ETIMEOUT), the outputs concerned are NaN, and the kernel finishes, so
+ * the CUDA context stays usable.  This self-test runs that wait on the GPU
+ * with a limit of limit_us microseconds (1 .. 10^7) on an mbarrier that
+ * nothing arrives on: it returns VBDR_ETIMEOUT once every thread of the probe
+ * gave up, VBDR_OK if the wait completed (it cannot), VBDR_EINVAL for a bad
+ * limit and VBDR_ECUDA on a CUDA error.  Synchronous.  Not part of the
+ * paper: it only tests the library's own error path. */
+VBDR_API int vbdr_selftest_bounded_wait(uint32_t limit_us, void *stream);
+
 VBDR_API const char *vbdr_strerror(int status);
 
 #ifdef __cplusplus

@@ -31,6 +31,7 @@
 // expires sets the plan's error word, the producer first waits (bounded) for
 // its copies in flight, and the block's outputs are written as NaN.
 #include "vbdr_internal.cuh"
+#include "tc_sm100.cuh"
 
 namespace vbk {
 namespace {
@@ -41,56 +42,13 @@ constexpr int kConsumerWarps = 31;
 constexpr int kPlanThreads = (kConsumerWarps + 1) * 32;
 constexpr int kBuildThreads = 1024;
 constexpr uint32_t kChunkBytes = (uint32_t)kPlanChunk;
-constexpr uint64_t kWaitLimitNs = 200000000ull;  // 0.2 s: a wait this long is a failure
-constexpr uint32_t kSuspendNs = 20000;           // suspend hint of one try_wait round
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(done)
-      : "r"(smem_addr(b)), "r"(parity), "n"(kSuspendNs)
-      : "memory");
-  return done != 0;
-}
-// Wait for the phase of parity `parity` to complete.  Each round may park
-// the warp (suspend hint) instead of spinning on the shared-memory pipe;
-// false once the wait has lasted kWaitLimitNs.
+// Every mbarrier wait gives up after this long (a wait that long is a failure).
+constexpr uint64_t kPlanWaitNs = 200000000ull;
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-  if (mbar_try(b, parity)) return true;
-  const uint64_t t0 = global_ns();
-  do {
-    if (mbar_try(b, parity)) return true;
-  } while (global_ns() - t0 < kWaitLimitNs);
-  return false;
+  return tc_mbar_wait(b, parity, kPlanWaitNs);
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
-               : "memory");
-}
-// TMA bulk copy global -> shared, completing `bytes` transactions on b.
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(b))
-      : "memory");
-}
+
 __device__ __forceinline__ uint4 ld_stream(const uint4 *p) {
   uint4 v;
   asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -193,10 +151,9 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     S.acc[0][i] = S.acc[1][i] = S.acc[2][i] = 0;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kPlanSlots; ++i) {
-      mbar_init(&S.full[i], 1);
-      mbar_init(&S.empty[i], kConsumerWarps);
+      tc_mbar_init(&S.full[i], 1);
+      tc_mbar_init(&S.empty[i], kConsumerWarps);
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     S.nZZ = pool_noise(d, s, c);
     S.bad = 0;
   }
@@ -217,9 +174,9 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
         }
         const unsigned long long ne = goff[ch + 1] - goff[ch];
         const uint32_t ebytes = 4u * (uint32_t)(ne < kEntCap ? ne : kEntCap);
-        mbar_expect_tx(&S.full[slot], kChunkBytes + ebytes);
-        bulk_load(S.ring[slot], s.reg + (uint64_t)ch * kChunkBytes, kChunkBytes, &S.full[slot]);
-        if (ebytes) bulk_load(S.ents[slot], p.entries + goff[ch], ebytes, &S.full[slot]);
+        tc_mbar_expect_tx(&S.full[slot], kChunkBytes + ebytes);
+        tc_bulk_load(S.ring[slot], s.reg + (uint64_t)ch * kChunkBytes, kChunkBytes, &S.full[slot]);
+        if (ebytes) tc_bulk_load(S.ents[slot], p.entries + goff[ch], ebytes, &S.full[slot]);
         issued = ch + 1;
       }
       // every issued copy lands before the block may finish
@@ -261,7 +218,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
         take(ring, acc, e.w);
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.empty[slot]);
+      if (lane == 0) tc_mbar_arrive(&S.empty[slot]);
     }
   }
   __syncthreads();

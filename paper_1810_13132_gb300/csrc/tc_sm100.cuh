@@ -1,6 +1,7 @@
 // tc_sm100.cuh -- inline-PTX wrappers for the 5th-generation tensor cores
-// (tcgen05: MMA with the accumulator in tensor memory), mbarriers and the
-// shared-memory matrix descriptors they read, as used by the MLP kernels.
+// (tcgen05: MMA with the accumulator in tensor memory), the shared-memory
+// matrix descriptors they read, mbarriers and TMA bulk copies (MLP and
+// planned-estimate kernels).
 //
 // Operand layout ("canonical K-major, no swizzle"): a matrix of R rows and K
 // bf16 columns (K a multiple of 8) is stored as 8x8 core matrices of 128
@@ -110,6 +111,26 @@ __device__ __forceinline__ void tc_mbar_init(uint64_t *b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem_addr(b)), "r"(count)
                : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem_addr(b)) : "memory");
+}
+// One arrival that also expects `bytes` of asynchronous-copy transactions.
+__device__ __forceinline__ void tc_mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_addr(b)),
+               "r"(bytes)
+               : "memory");
+}
+// TMA bulk copy global -> shared (16-byte aligned, a multiple of 16 bytes),
+// completing its bytes on the mbarrier b.
+__device__ __forceinline__ void tc_bulk_load(void *dst, const void *src, uint32_t bytes,
+                                             uint64_t *b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc_smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(tc_smem_addr(b))
+      : "memory");
 }
 
 // Wait for the completion of the phase of parity `parity`, parking the warp

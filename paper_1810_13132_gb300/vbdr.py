@@ -49,6 +49,7 @@ _SIGS = {
     "vbdr_copy_pool_sums_alt": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64),
                                                _VP]),
     "vbdr_copy_pcsa": (ctypes.c_int, [_VP, _VP, _VP]),
+    "vbdr_selftest_bounded_wait": (ctypes.c_int, [_U32, _VP]),
     "vbdr_plan_create": (ctypes.c_int, [_VP, _VP, _U64, ctypes.POINTER(_VP), _VP]),
     "vbdr_plan_destroy": (ctypes.c_int, [_VP]),
     "vbdr_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64),

@@ -72,6 +72,7 @@ def test_null_handle_calls(lib):
     assert lib.vbdr_estimate_alt(None, None, 0, None, 1, None) == -1
     assert lib.vbdr_copy_pool_sums_alt(None, None, None, None) == -1
     assert lib.vbdr_copy_pcsa(None, None, None) == -1
+    assert lib.vbdr_selftest_bounded_wait(0, None) == -1  # refused before any CUDA call
     assert lib.vbdr_plan_create(None, None, 0, None, None) == -1
     assert lib.vbdr_plan_destroy(None) == 0
     assert lib.vbdr_plan_info(None, None, None, None) == -1
