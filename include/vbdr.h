@@ -447,6 +447,16 @@ VBDR_API int vbdr_copy_pool_sums_alt(vbdr_t h, uint64_t *L_Z, uint64_t *P_Z, voi
 VBDR_API int vbdr_copy_pcsa(vbdr_t h, uint8_t *h_pcsa, void *stream);
 
 /* Human-readable text of a vbdr_status. */
+/* Bounds checks.  The library built with -DVBDR_CHECK (libvbdr_check.so,
+ * next to libvbdr.so) tests every physical index, LBP1 and register value in
+ * its kernels, skips an access that would leave its buffer and records it:
+ * *flags receives the violations seen by this handle's kernels (bit 0: a
+ * physical index >= Z, bit 1: an LBP1 > R, bit 2: a register value out of
+ * range, bit 3: a planned-estimate entry out of range; always 0 in the
+ * normal build) and *checked_build (may be NULL) whether the checks are
+ * compiled in.  Synchronous.  Errors: VBDR_EINVAL, VBDR_ECUDA. */
+VBDR_API int vbdr_check_flags(vbdr_t h, uint32_t *flags, int *checked_build);
+
 /* Failure detection of the device-side waits.  The planned estimate and the
  * MLP kernels wait on mbarriers with a bounded wait (0.2 s): a wait that
  * expires sets the kernel's error word (vbdr_plan_status reports

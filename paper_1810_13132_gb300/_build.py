@@ -3,6 +3,12 @@
 Each .cu translation unit is compiled in parallel with nvcc
 (-gencode arch=compute_103a,code=sm_103a), then linked into one shared
 library next to this file.  A stamp of the sources and flags skips rebuilds.
+
+check=True builds the bounds-checked variant libvbdr_check.so (-DVBDR_CHECK):
+every kernel verifies its indices and register values, skips an access that
+would leave its buffer and records it in the handle's check flags
+(vbdr_check_flags).  It stands in for a race / bounds sanitizer, which is not
+available here.
 """
 from __future__ import annotations
 
@@ -16,6 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libvbdr.so")
+LIB_CHECK = os.path.join(HERE, "libvbdr_check.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -45,20 +52,24 @@ def _stamp(extra: list[str]) -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile libvbdr.so if its sources changed; returns its path."""
-    extra = list(extra_flags or [])
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          check: bool = False) -> str:
+    """Compile libvbdr.so (or libvbdr_check.so) if its sources changed;
+    returns its path."""
+    extra = list(extra_flags or []) + (["-DVBDR_CHECK"] if check else [])
+    lib = LIB_CHECK if check else LIB
+    obj_dir = os.path.join(BUILD_DIR, "check" if check else "release")
     stamp = _stamp(extra)
-    stamp_file = LIB + ".stamp"
-    if (not force and os.path.exists(LIB) and os.path.exists(stamp_file)
+    stamp_file = lib + ".stamp"
+    if (not force and os.path.exists(lib) and os.path.exists(stamp_file)
             and open(stamp_file).read() == stamp):
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+        return lib
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
     srcs = _sources()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-I", os.path.join(ROOT, "include"),
                "-c", src, "-o", obj]
         if verbose:
@@ -72,17 +83,17 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp_file, "w") as f:
         f.write(stamp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check="--check" in sys.argv))

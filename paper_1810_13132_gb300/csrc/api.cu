@@ -71,6 +71,7 @@ __global__ void init_kernel(Dims d, DevState s, uint32_t word_init, uint32_t kta
     s.ktab[i] = vbk::make_kent(vbk::mix64(s1));
   }
   if (tid < vbk::kSums) s.sums[tid] = 0ull;
+  if (tid == 0) *s.check = 0u;
   if (s.pcsa)
     for (uint64_t j = tid; j < d.Zs; j += stride) s.pcsa[j] = 0u;
 }
@@ -133,6 +134,7 @@ void free_state(vbdr *h) {
   cudaFree(h->s.ktab);
   cudaFree(h->s.lnv);
   cudaFree(h->s.sums);
+  cudaFree(h->s.check);
   for (int i = 0; i < 2; ++i) {
     cudaFree(h->stage[i]);
     if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
@@ -224,6 +226,7 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->s.ktab, (size_t)kn * sizeof(vbk::KEnt));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.lnv, vbk::kLnTab * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.sums, vbk::kSums * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->s.check, sizeof(unsigned int));
   if (e == cudaSuccess) {
     double lnv[vbk::kLnTab];
     lnv[0] = 0.0;
@@ -667,6 +670,17 @@ int vbdr_copy_pool_sums(vbdr_t h, uint64_t *S_Z, uint64_t *V_Z, void *stream) {
   if (e != cudaSuccess) return fail_cuda(h, e);
   *S_Z = v[0];
   *V_Z = v[1];
+  return VBDR_OK;
+}
+
+int vbdr_check_flags(vbdr_t h, uint32_t *flags, int *checked_build) {
+  if (!h || !flags) return VBDR_EINVAL;
+  if (checked_build) *checked_build = vbk::kChecked ? 1 : 0;
+  if (h->sticky) return h->sticky;
+  unsigned int v = 0;
+  cudaError_t e = cudaMemcpy(&v, h->s.check, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail_cuda(h, e);
+  *flags = v;
   return VBDR_OK;
 }
 

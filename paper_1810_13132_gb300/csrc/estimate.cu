@@ -111,7 +111,10 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
           M[u] = 0xffu;
           if (i < g) {
             const uint32_t pidx = reduce32(hash32(aip, kt[i]), d.zmul);
-            M[u] = __ldg(vals + pidx);
+            if (vbk_check(pidx < d.Z, s.check, kChkPidx)) {
+              M[u] = __ldg(vals + pidx);
+              if (!vbk_check(M[u] <= 32u, s.check, kChkReg)) M[u] = 0xffu;
+            }
           }
         }
 #pragma unroll

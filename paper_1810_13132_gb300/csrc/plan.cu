@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kBuildThreads)
     const uint32_t g = 1u << host_b(d, aip);
     for (uint32_t i = lane; i < g; i += 32) {
       const uint32_t pidx = reduce32(hash32(aip, s.ktab[i]), d.zmul);
+      if (!vbk_check(pidx < d.Z, s.check, kChkPidx)) continue;
       atomicAdd(&cnt[pidx >> kPlanChunkLog2], 1u);
     }
   }
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(kBuildThreads)
     const uint32_t g = 1u << host_b(d, aip);
     for (uint32_t i = lane; i < g; i += 32) {
       const uint32_t pidx = reduce32(hash32(aip, s.ktab[i]), d.zmul);
+      if (!vbk_check(pidx < d.Z, s.check, kChkPidx)) continue;
       const uint32_t c = pidx >> kPlanChunkLog2;
       const uint32_t slot = atomicAdd(&cur[c], 1u);
       p.entries[goff[c] + slot] = (h << kPlanChunkLog2) | (pidx & (kChunkBytes - 1));
@@ -134,8 +136,10 @@ static_assert(sizeof(PlanSmem) <= 227 * 1024, "shared memory of one CTA");
 // 1 << ((16 - M) & 15) is 1, 2^(16-M) or 2^(32-M) respectively.
 // The two min() keep every access inside the accumulators whatever the
 // entry or register value.
-__device__ __forceinline__ void take(const unsigned char *ring, uint32_t *acc, uint32_t e) {
+__device__ __forceinline__ void take(const unsigned char *ring, uint32_t *acc, uint32_t e,
+                                     unsigned int *chk) {
   const uint32_t M = ring[e & (kChunkBytes - 1)];
+  if (!vbk_check(M <= 32u && (e >> kPlanChunkLog2) <= kPlanMaxHB, chk, kChkPlan)) return;
   const uint32_t which = min((M + 15u) >> 4, 2u);
   const uint32_t lh = min(e >> kPlanChunkLog2, kPlanMaxHB);
   atomicAdd(acc + which * kAccRow + lh, 1u << ((16u - M) & 15u));
@@ -203,19 +207,19 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       const uint32_t lead = (t + 160u * ch) % T;
       for (uint32_t q = lead; q < nq_s; q += T) {
         const uint4 e = S.ents[slot][q];
-        take(ring, acc, e.x);
-        take(ring, acc, e.y);
-        take(ring, acc, e.z);
-        take(ring, acc, e.w);
+        take(ring, acc, e.x, s.check);
+        take(ring, acc, e.y, s.check);
+        take(ring, acc, e.z, s.check);
+        take(ring, acc, e.w, s.check);
       }
       // a group larger than the staging slot: the rest from global memory
       const uint4 *grp = reinterpret_cast<const uint4 *>(p.entries) + q0;
       for (uint64_t q = nq_s + lead; q < nq; q += T) {
         const uint4 e = ld_stream(grp + q);
-        take(ring, acc, e.x);
-        take(ring, acc, e.y);
-        take(ring, acc, e.z);
-        take(ring, acc, e.w);
+        take(ring, acc, e.x, s.check);
+        take(ring, acc, e.y, s.check);
+        take(ring, acc, e.z, s.check);
+        take(ring, acc, e.w, s.check);
       }
       __syncwarp();
       if (lane == 0) tc_mbar_arrive(&S.empty[slot]);

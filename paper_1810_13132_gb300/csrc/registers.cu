@@ -42,7 +42,9 @@ __global__ void __launch_bounds__(kThreads)
     const uint8_t *v = vregs + offsets[h];
     for (uint32_t i = lane; i < g; i += 32) {
       const uint32_t val = v[i];
-      if (val) byte_max(s.reg, reduce32(hash32(aip, s.ktab[i]), d.zmul), val);
+      const uint32_t pidx = reduce32(hash32(aip, s.ktab[i]), d.zmul);
+      if (val && vbk_check(pidx < d.Z, s.check, kChkPidx) && vbk_check(val <= d.R, s.check, kChkReg))
+        byte_max(s.reg, pidx, val);
     }
   }
 }

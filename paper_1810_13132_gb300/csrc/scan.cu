@@ -64,13 +64,19 @@ __device__ __forceinline__ void red_and(uint32_t *p, uint32_t v) {
 //   serial: word = pidx (byte of nowLBP1), mask = LBP1 (the value to max in)
 template <int W, bool MIXED>
 __device__ __forceinline__ void pair_update(const Dims &d, const KEnt *kt, uint32_t aip,
-                                            uint32_t bip, uint64_t &word, uint32_t &mask) {
+                                            uint32_t bip, uint64_t &word, uint32_t &mask,
+                                            unsigned int *chk) {
   const uint32_t b = MIXED ? d.b_min + (aip >> 30) : d.b;
   const uint32_t bipp = hash32(bip, d.K1);
   const uint32_t vidx = bipp >> (32 - b);
   const uint32_t x = bipp << b;
   const uint32_t r0 = min((uint32_t)__clz(x), 31u - b);  // LBP1 - 1
   const uint32_t pidx = reduce32(hash32(aip, kt[vidx]), d.zmul);
+  if (!vbk_check(pidx < d.Z, chk, kChkPidx) || !vbk_check(r0 < d.R, chk, kChkRho)) {
+    word = 0;
+    mask = 0u;  // bounds-checked build: no update
+    return;
+  }
   if constexpr (W == 0) {
     word = pidx;
     mask = 1u << r0;
@@ -133,8 +139,8 @@ __global__ void __launch_bounds__(kScanThreads)
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const bool ok = base + (uint64_t)u * stride < units;
-      pair_update<W, MIXED>(d, kt, v[u].x, v[u].y, word[2 * u], mask[2 * u]);
-      pair_update<W, MIXED>(d, kt, v[u].z, v[u].w, word[2 * u + 1], mask[2 * u + 1]);
+      pair_update<W, MIXED>(d, kt, v[u].x, v[u].y, word[2 * u], mask[2 * u], s.check);
+      pair_update<W, MIXED>(d, kt, v[u].z, v[u].w, word[2 * u + 1], mask[2 * u + 1], s.check);
       if (!ok) mask[2 * u] = mask[2 * u + 1] = 0u;
       // adjacent pairs of one load on the same word: one update
       if (word[2 * u] == word[2 * u + 1]) {
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(kScanThreads)
     const uint32_t *p = reinterpret_cast<const uint32_t *>(pairs2) + 2 * (n_pairs - 1);
     uint64_t word;
     uint32_t mask;
-    pair_update<W, MIXED>(d, kt, p[0], p[1], word, mask);
+    pair_update<W, MIXED>(d, kt, p[0], p[1], word, mask, s.check);
     if constexpr (W == 0)
       red_or(state + word, mask);
     else if constexpr (W < 0)

@@ -127,7 +127,27 @@ struct DevState {
   double *lnv;       // [kLnTab] ln(v)
   unsigned long long *sums;  // [kSums]: pool sums of the last slide and the
                              // partials of their reduction (kSum* below)
+  unsigned int *check;       // bounds-checked build: violations seen (kChk*)
 };
+
+// Bounds-checked build (-DVBDR_CHECK): kernels test their indices and
+// register values, skip an access that would leave its buffer and record
+// the violation in DevState::check.  In the normal build vbk_check is the
+// constant true and the tests vanish.
+#ifdef VBDR_CHECK
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+enum : unsigned int { kChkPidx = 1u, kChkRho = 2u, kChkReg = 4u, kChkPlan = 8u };
+__device__ __forceinline__ bool vbk_check(bool ok, unsigned int *flags, unsigned int bit) {
+  if constexpr (kChecked) {
+    if (!ok && flags) atomicOr(flags, bit);
+    return ok;
+  } else {
+    return true;
+  }
+}
 
 // Slots of DevState::sums.  Totals: S_Z = sum 2^(32 - reg), V_Z = #{reg = 0},
 // L_Z = sum reg (LogLog), P_Z = sum pcsa (PCSA); each has a partial that the

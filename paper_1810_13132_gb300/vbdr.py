@@ -50,6 +50,7 @@ _SIGS = {
                                                _VP]),
     "vbdr_copy_pcsa": (ctypes.c_int, [_VP, _VP, _VP]),
     "vbdr_selftest_bounded_wait": (ctypes.c_int, [_U32, _VP]),
+    "vbdr_check_flags": (ctypes.c_int, [_VP, ctypes.POINTER(_U32), ctypes.POINTER(ctypes.c_int)]),
     "vbdr_plan_create": (ctypes.c_int, [_VP, _VP, _U64, ctypes.POINTER(_VP), _VP]),
     "vbdr_plan_destroy": (ctypes.c_int, [_VP]),
     "vbdr_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64),
@@ -101,15 +102,21 @@ _SIGS = {
 _lib = None
 
 
+def _checked() -> bool:
+    # VBDR_CHECKED=1 selects the bounds-checked build (libvbdr_check.so)
+    return os.environ.get("VBDR_CHECKED", "") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECK if _checked() else _build.LIB
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libvbdr.so (building it with nvcc first if it is missing)."""
+    """Load libvbdr.so, or libvbdr_check.so when VBDR_CHECKED=1 (building
+    it with nvcc first if it is missing)."""
     global _lib
     if _lib is None:
-        path = _build.build() if build_if_missing else _build.LIB
+        path = _build.build(check=_checked()) if build_if_missing else library_path()
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA library missing: {path}")
         L = ctypes.CDLL(path)
@@ -347,6 +354,13 @@ class Vbdr:
         _check("vbdr_copy_pool_sums_alt", self._L.vbdr_copy_pool_sums_alt(
             self._h, ctypes.byref(L), ctypes.byref(P), _stream_ptr(stream)))
         return L.value, P.value
+
+    def check_flags(self) -> tuple[int, bool]:
+        """(violations recorded by the bounds-checked build, whether this
+        library is that build)."""
+        f, c = _U32(), ctypes.c_int()
+        _check("vbdr_check_flags", self._L.vbdr_check_flags(self._h, ctypes.byref(f), ctypes.byref(c)))
+        return f.value, bool(c.value)
 
     def pcsa_statistics(self, stream=None) -> np.ndarray:
         """PCSA statistic of every physical BDR at the last slide (gsmall)."""
