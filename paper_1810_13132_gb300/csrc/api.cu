@@ -8,10 +8,24 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/vbdr.h"
 #include "vbdr_internal.cuh"
 
 using vbk::DevState;
+
+namespace {
+// NVTX range over an entry point (tracing tools show the library's calls on
+// the timeline beside its kernels; without a tool attached it costs a
+// branch).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 using vbk::Dims;
 using vbk::EstConst;
 
@@ -270,6 +284,7 @@ int vbdr_get_dims(vbdr_t h, uint32_t *R, uint32_t *w, uint32_t *words) {
 }
 
 int vbdr_scan_slice(vbdr_t h, const uint32_t *d_pairs, uint64_t n, void *stream) {
+  NvtxRange nvtx("vbdr_scan_slice");
   if (!h) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (n == 0) return VBDR_OK;
@@ -280,6 +295,7 @@ int vbdr_scan_slice(vbdr_t h, const uint32_t *d_pairs, uint64_t n, void *stream)
 
 int vbdr_scan_slice_devn(vbdr_t h, const uint32_t *d_pairs, const uint64_t *d_n,
                          uint64_t max_n, void *stream) {
+  NvtxRange nvtx("vbdr_scan_slice_devn");
   if (!h) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (max_n == 0) return VBDR_OK;
@@ -289,6 +305,7 @@ int vbdr_scan_slice_devn(vbdr_t h, const uint32_t *d_pairs, const uint64_t *d_n,
 }
 
 int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n, void *stream) {
+  NvtxRange nvtx("vbdr_scan_slice_host");
   if (!h) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (n == 0) return VBDR_OK;
@@ -339,6 +356,7 @@ int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n, void *st
 }
 
 int vbdr_slide(vbdr_t h, void *stream) {
+  NvtxRange nvtx("vbdr_slide");
   if (!h) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   int rc = fail_cuda(h, vbk::launch_slide(h->d, h->s, h->layout,
@@ -349,6 +367,7 @@ int vbdr_slide(vbdr_t h, void *stream) {
 
 int vbdr_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n, float *d_out,
                   void *stream) {
+  NvtxRange nvtx("vbdr_estimate");
   if (!h) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (!h->slid) return VBDR_EORDER;
@@ -361,6 +380,7 @@ int vbdr_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n, float *d_out,
 
 int vbdr_estimate_alt(vbdr_t h, const uint32_t *d_aips, uint64_t n, float *d_out,
                       int estimator, void *stream) {
+  NvtxRange nvtx("vbdr_estimate_alt");
   if (!h) return VBDR_EINVAL;
   if (estimator == VBDR_EST_HLL) return vbdr_estimate(h, d_aips, n, d_out, stream);
   if (estimator != VBDR_EST_LOGLOG && estimator != VBDR_EST_PCSA) return VBDR_EINVAL;
@@ -376,6 +396,7 @@ int vbdr_estimate_alt(vbdr_t h, const uint32_t *d_aips, uint64_t n, float *d_out
 
 int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n, float *h_out,
                        void *stream) {
+  NvtxRange nvtx("vbdr_estimate_host");
   if (!h) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (!h->slid) return VBDR_EORDER;
@@ -407,6 +428,7 @@ int vbdr_estimate_host(vbdr_t h, const uint32_t *h_aips, uint64_t n, float *h_ou
 
 int vbdr_features(vbdr_t h, const uint32_t *d_aips, uint64_t n, uint16_t *d_X, float *d_plain,
                   void *stream) {
+  NvtxRange nvtx("vbdr_features");
   if (!h) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (!h->slid) return VBDR_EORDER;
@@ -425,6 +447,7 @@ int vbdr_features(vbdr_t h, const uint32_t *d_aips, uint64_t n, uint16_t *d_X, f
 
 int vbdr_estimate_learned(vbdr_t h, vbdr_mlp_t m, const uint32_t *d_aips, uint64_t n,
                           float *d_out, void *stream) {
+  NvtxRange nvtx("vbdr_estimate_learned");
   if (!h || !m) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (!h->slid) return VBDR_EORDER;
@@ -458,6 +481,7 @@ int vbdr_estimate_learned(vbdr_t h, vbdr_mlp_t m, const uint32_t *d_aips, uint64
 
 int vbdr_load_virtual_registers(vbdr_t h, const uint32_t *d_aips, const uint64_t *d_offsets,
                                 uint64_t n_hosts, const uint8_t *d_vregs, void *stream) {
+  NvtxRange nvtx("vbdr_load_virtual_registers");
   if (!h) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (n_hosts && (!d_aips || !d_offsets || !d_vregs)) return VBDR_EINVAL;
@@ -482,6 +506,7 @@ int vbdr_set_estimate_launch(vbdr_t h, uint32_t lanes, uint32_t threads) {
 
 int vbdr_autotune_estimate(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts, float *d_out,
                            uint32_t *lanes, uint32_t *threads, void *stream) {
+  NvtxRange nvtx("vbdr_autotune_estimate");
   if (!h) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (!h->slid) return VBDR_EORDER;
@@ -561,6 +586,7 @@ int vbdr_state_bytes(vbdr_t h, uint64_t *bytes) {
 }
 
 int vbdr_save(vbdr_t h, void *h_buf, uint64_t cap, void *stream) {
+  NvtxRange nvtx("vbdr_save");
   if (!h || !h_buf) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   uint64_t need = 0;
@@ -589,6 +615,7 @@ int vbdr_save(vbdr_t h, void *h_buf, uint64_t cap, void *stream) {
 }
 
 int vbdr_load(vbdr_t h, const void *h_buf, uint64_t len, void *stream) {
+  NvtxRange nvtx("vbdr_load");
   if (!h || !h_buf) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   uint64_t need = 0;
@@ -711,6 +738,7 @@ int vbdr_copy_pcsa(vbdr_t h, uint8_t *h_pcsa, void *stream) {
 
 int vbdr_plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n, vbdr_plan_t *out,
                      void *stream) {
+  NvtxRange nvtx("vbdr_plan_create");
   if (!h || !out) return VBDR_EINVAL;
   *out = nullptr;
   if (h->sticky) return h->sticky;
@@ -831,6 +859,7 @@ bool plan_matches(const vbdr *h, const vbdr_plan *p) {
 }  // namespace
 
 int vbdr_estimate_planned(vbdr_t h, vbdr_plan_t p, float *d_out, void *stream) {
+  NvtxRange nvtx("vbdr_estimate_planned");
   if (!h || !p) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (!plan_matches(h, p)) return VBDR_EINVAL;
@@ -842,6 +871,7 @@ int vbdr_estimate_planned(vbdr_t h, vbdr_plan_t p, float *d_out, void *stream) {
 }
 
 int vbdr_estimate_planned_host(vbdr_t h, vbdr_plan_t p, float *h_out, void *stream) {
+  NvtxRange nvtx("vbdr_estimate_planned_host");
   if (!h || !p) return VBDR_EINVAL;
   if (h->sticky) return h->sticky;
   if (!plan_matches(h, p)) return VBDR_EINVAL;
