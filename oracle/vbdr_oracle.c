@@ -327,12 +327,17 @@ double orc_hll(double m, uint64_t S, uint64_t V) {
 }
 
 /* vHLL with virtual register sharing. */
-double orc_vhll(double Z, double g, uint64_t S, uint64_t V, uint64_t S_Z,
-                uint64_t V_Z) {
-  double n_g = orc_hll(g, S, V);
-  double n_Z = orc_hll(Z, S_Z, V_Z);
+/* The virtual-sharing noise removal of vHLL, n = Z g / (Z - g) (n_g / g -
+ * n_Z / Z) clamped at 0, for any estimator of the host's registers (n_g)
+ * and of the pool (n_Z). */
+static double orc_denoise(double Z, double g, double n_g, double n_Z) {
   double n = (Z * g / (Z - g)) * (n_g / g - n_Z / Z);
   return n > 0.0 ? n : 0.0;
+}
+
+double orc_vhll(double Z, double g, uint64_t S, uint64_t V, uint64_t S_Z,
+                uint64_t V_Z) {
+  return orc_denoise(Z, g, orc_hll(g, S, V), orc_hll(Z, S_Z, V_Z));
 }
 
 /* LogLog bias constant (Durand & Flajolet 2003):
@@ -352,12 +357,6 @@ double orc_loglog(double m, uint64_t L) {
  * 1985, phi = 0.77351). */
 double orc_pcsa(double m, uint64_t P) {
   return m / 0.77351 * exp2((double)P / m);
-}
-
-/* The virtual-sharing noise removal of vHLL applied to any estimate pair. */
-static double orc_denoise(double Z, double g, double n_g, double n_Z) {
-  double n = (Z * g / (Z - g)) * (n_g / g - n_Z / Z);
-  return n > 0.0 ? n : 0.0;
 }
 
 /* Alg. 5 getSumLBP1 generalised: visits the host's g virtual registers

@@ -2,8 +2,9 @@
 
 Each case below plants one plausible mistake in a copy of the oracle's C
 source (a dropped term, a wrong sign or index, an off-by-one, a swapped
-operand), builds it on the CPU, and runs the pin suite (test_oracle.py)
-against it in a fresh process.  Every mutant must make that suite fail.
+operand), builds it on the CPU, and runs the pin suites (test_oracle.py and
+test_oracle_alt.py) against it in a fresh process.  Every mutant must make
+them fail.
 """
 import os
 import subprocess
@@ -33,8 +34,10 @@ MUTANTS = {
                              "if (((o->bs[j] >> i) & 1u) && lbp1 == 0) lbp1 = i + 1;"),
     "gfast_bs_not_cleared": ("      o->bs[j] = 0;\n", "\n"),
     "gsmall_age_before_read": (
-        "      o->reg[j] = (uint8_t)GetLBP1BDR(o, j);\n      for (uint32_t r = 1; r <= o->R; ++r) SlideDR(o, &drv[r]);",
-        "      for (uint32_t r = 1; r <= o->R; ++r) SlideDR(o, &drv[r]);\n      o->reg[j] = (uint8_t)GetLBP1BDR(o, j);"),
+        "      o->reg[j] = (uint8_t)GetLBP1BDR(o, j);\n      o->pcsa[j] = (uint8_t)PcsaBDR(o, j);\n"
+        "      for (uint32_t r = 1; r <= o->R; ++r) SlideDR(o, &drv[r]);",
+        "      for (uint32_t r = 1; r <= o->R; ++r) SlideDR(o, &drv[r]);\n"
+        "      o->reg[j] = (uint8_t)GetLBP1BDR(o, j);\n      o->pcsa[j] = (uint8_t)PcsaBDR(o, j);"),
     "serial_no_reset": ("      o->now[j] = 0;\n", "\n"),
     "alpha_64": ("if (m == 64) return 0.709;", "if (m == 64) return 0.697;"),
     "lc_threshold": ("if (E <= 2.5 * m && V > 0)", "if (E <= 0.5 * m && V > 0)"),
@@ -46,6 +49,17 @@ MUTANTS = {
                       "double n = (Z * g / (Z + g)) * (n_g / g - n_Z / Z);"),
     "harmonic_exponent": ("s += 1ULL << (32 - M);", "s += 1ULL << (31 - M);"),
     "dr_width_short": ("while ((1u << w) < k + 1) ++w;", "while ((1u << w) < k) ++w;"),
+    # LogLog / PCSA (pins in test_oracle_alt.py)
+    "loglog_alpha_exponent": ("return pow(base, -m);", "return pow(base, m);"),
+    "loglog_mean_not_divided": ("return orc_loglog_alpha(m) * m * exp2((double)L / m);",
+                                "return orc_loglog_alpha(m) * m * exp2((double)L);"),
+    "pcsa_phi_inverted": ("return m / 0.77351 * exp2((double)P / m);",
+                          "return m * 0.77351 * exp2((double)P / m);"),
+    "pcsa_highest_active": ("    if (!IsActiveDR(o, drv[r])) return r - 1;\n  return o->R;",
+                            "    if (IsActiveDR(o, drv[r])) return r;\n  return 0;"),
+    "pcsa_read_after_aging": (
+        "      o->pcsa[j] = (uint8_t)PcsaBDR(o, j);\n      for (uint32_t r = 1; r <= o->R; ++r) SlideDR(o, &drv[r]);",
+        "      for (uint32_t r = 1; r <= o->R; ++r) SlideDR(o, &drv[r]);\n      o->pcsa[j] = (uint8_t)PcsaBDR(o, j);"),
 }
 
 
@@ -68,6 +82,6 @@ def test_pins_catch_mutant(tmp_path, name):
     so = _build(tmp_path, name, old, new)
     env = dict(os.environ, ORACLE_LIB_OVERRIDE=so)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(HERE, "test_oracle.py")],
+                        os.path.join(HERE, "test_oracle.py"), os.path.join(HERE, "test_oracle_alt.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
