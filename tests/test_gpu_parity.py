@@ -80,6 +80,7 @@ def _run(layout, k, Z, b, slices, aips, b_min=None, group_rule=0, every=True,
             _compare_state(v, o, f"t={t}")
     _compare_estimates(v, o, aips)
     v.close()
+    return o
 
 
 def _compare_state_scan(v, o, tag):
@@ -148,6 +149,28 @@ def test_max_contention_one_host(layout):
     aip = np.array([0xDEADBEEF], dtype=np.uint32)
     slices = [traffic.uniform_pairs(rng, 300_000, aip) for _ in range(3)]
     _run(layout, 3, 1000, 1, slices, aip)
+
+
+@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
+def test_lbp1_at_the_cap(layout):
+    """Pairs whose shifted hash word is all zero below the virtual-index bits
+    (LBP1 = R = 32 - b, the capped case), found by brute force over bips with
+    the oracle's hash, mixed with ordinary pairs: the DR at the cap and the
+    registers equal to R must match the oracle."""
+    b, Z = 15, (1 << 17) + 5
+    h = oracle.Oracle(layout, k=3, Z=Z, b=b, seed=SEED)
+    aips = np.array([0x0A0B0C0D, 0x7F000001], dtype=np.uint32)
+    capped = [(int(a), bip) for a in aips for bip in range(0, 400_000)
+              if h.hash_pair(int(a), bip)[1] == 32 - b]
+    assert len(capped) >= 4
+    rng = np.random.default_rng(108)
+    slices = []
+    for t in range(4):
+        s = np.concatenate([np.array(capped[t::2], dtype=np.uint32).reshape(-1, 2),
+                            traffic.uniform_pairs(rng, 5000, aips)])
+        slices.append(s)
+    o = _run(layout, 3, Z, b, slices, aips)
+    assert (o.state()["reg"] == 32 - b).any()
 
 
 @pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
