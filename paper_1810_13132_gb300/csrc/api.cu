@@ -121,6 +121,7 @@ void fill_est_const(const Dims &d, EstConst *c) {
     const double g = (double)(1u << b);
     c->ll[b] = b ? loglog_alpha(g) * g : 0.0;
     c->pc[b] = g / kPcsaPhi;
+    c->inv_g[b] = std::ldexp(1.0, -b);
   }
   c->ll_Z = loglog_alpha(Z) * Z;
   c->pc_Z = Z / kPcsaPhi;

@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
       if constexpr (SUM) {
         // n_g = const_g 2^(sum / g); n = Z g / (Z - g) (n_g / g - n_Z / Z)
         const double base = MODE == kLogLog ? c.ll[b] : c.pc[b];
-        n_g = base * exp2(ldexp((double)myS, -(int)b));
-        est = c.kz[b] * (ldexp(n_g, -(int)b) - nZZ);
+        n_g = base * exp2((double)myS * c.inv_g[b]);
+        est = c.kz[b] * (n_g * c.inv_g[b] - nZZ);
         if (!(est > 0.0)) est = 0.0;
       } else {
         est = host_estimate(myS, myV, b, c, lnv_s, nZZ, &n_g);

@@ -140,13 +140,14 @@ extern "C" int vbdr_estimate_registers_noalloc(const uint8_t *d_reg, uint64_t nu
   s.ktab = sc->ktab;
   s.lnv = sc->lnv;
   s.sums = sc->sums;
-  EstConst c;
+  EstConst c = {};  // the plain estimate reads amm, kz, lng, inv_g and amm_Z
   const double Z = (double)num_bdr;
   for (int b = 0; b <= kMaxLog2G; ++b) {
     const double g = (double)(1u << b);
     c.amm[b] = hll_alpha_host(g) * g * g;
     c.kz[b] = Z * g / (Z - g);
     c.lng[b] = std::log(g);
+    c.inv_g[b] = std::ldexp(1.0, -b);
   }
   c.amm_Z = hll_alpha_host(Z) * Z * Z;
 

@@ -115,7 +115,12 @@ struct EstConst {
   double ll[kMaxLog2G + 1];
   double pc[kMaxLog2G + 1];
   double ll_Z, pc_Z;
+  double inv_g[kMaxLog2G + 1];  // 2^-b exactly
 };
+
+// 2^-32: S 2^-32 is the harmonic sum of 2^-M (a multiplication by a power of
+// two is exact, the same value as ldexp without its range handling).
+constexpr double kTwoM32 = 0x1p-32;
 
 struct DevState {
   uint32_t *drv;     // [P][Zs]
@@ -167,7 +172,7 @@ __device__ __forceinline__ uint32_t host_b(const Dims &d, uint32_t aip) {
 __device__ __forceinline__ double pool_noise(const Dims &d, const DevState &s, const EstConst &c) {
   const double Z = (double)d.Z;
   const unsigned long long S_Z = s.sums[0], V_Z = s.sums[1];
-  double E = c.amm_Z / ldexp((double)S_Z, -32);
+  double E = c.amm_Z / ((double)S_Z * kTwoM32);
   if (E <= 2.5 * Z && V_Z > 0) E = Z * log(Z / (double)V_Z);
   return E / Z;
 }
@@ -182,10 +187,10 @@ __device__ __forceinline__ double host_estimate(unsigned long long S, uint32_t V
                                                 const EstConst &c, const double *lnv, double nZZ,
                                                 double *n_g_out) {
   const double g = (double)(1u << b);
-  double n_g = c.amm[b] / ldexp((double)S, -32);
+  double n_g = c.amm[b] / ((double)S * kTwoM32);
   if (n_g <= 2.5 * g && V > 0)
     n_g = g * (V < (uint32_t)kLnTab ? c.lng[b] - lnv[V] : log(g / (double)V));
-  double est = c.kz[b] * (ldexp(n_g, -(int)b) - nZZ);
+  double est = c.kz[b] * (n_g * c.inv_g[b] - nZZ);
   if (!(est > 0.0)) est = 0.0;
   if (n_g_out) *n_g_out = n_g;
   return est;
