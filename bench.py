@@ -45,6 +45,7 @@ def _args():
     p.add_argument("--estimate", default="planned", choices=["planned", "gather"],
                    help="trace/small: estimate through a host-list plan (built once, outside "
                         "the timed steps) or by gathering every virtual register")
+    p.add_argument("--no-learned", action="store_true", help="serve: plain estimates only")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mre", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -559,7 +560,7 @@ def run_serve(a):
         tenants.append((st.aips, pool, sizes, offs))
     mlp = None
     wpath = os.path.join(ROOT, "paper_1810_13132_gb300", "weights", "correction_trace.npz")
-    if os.path.exists(wpath):
+    if os.path.exists(wpath) and not a.no_learned:
         wz = np.load(wpath)
         mlp = Mlp(seed=1)
         mlp.set_params(wz["params"], float(wz["nmax"]))

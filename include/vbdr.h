@@ -457,8 +457,8 @@ VBDR_API int vbdr_copy_pcsa(vbdr_t h, uint8_t *h_pcsa, void *stream);
  * compiled in.  Synchronous.  Errors: VBDR_EINVAL, VBDR_ECUDA. */
 VBDR_API int vbdr_check_flags(vbdr_t h, uint32_t *flags, int *checked_build);
 
-/* Failure detection of the device-side waits.  The planned estimate and the
- * MLP kernels wait on mbarriers with a bounded wait (0.2 s): a wait that
+/* Failure detection of the device-side waits.  The planned estimate waits
+ * on mbarriers (its TMA ring) with a bounded wait (0.2 s): a wait that
  * expires sets the kernel's error word (vbdr_plan_status reports
  * VBDR_ETIMEOUT), the outputs concerned are NaN, and the kernel finishes, so
  * the CUDA context stays usable.  This self-test runs that wait on the GPU

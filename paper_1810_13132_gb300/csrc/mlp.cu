@@ -16,7 +16,6 @@
 #include "../../include/vbdr.h"
 #include "mlp_device.cuh"
 #include "vbdr_internal.cuh"
-#include "tc_sm100.cuh"
 
 struct vbdr_mlp {
   float *theta;          // FP32 master parameters [kMlpParams]
@@ -24,7 +23,7 @@ struct vbdr_mlp {
   float *adam_m, *adam_v;
   __nv_bfloat16 *w1c;    // [64][48]
   __nv_bfloat16 *w2;     // [64][64]
-  unsigned int *err;     // set by an inference kernel whose wait expired
+  uint2 *w1f, *w2f;      // BF16 weights in mma fragment order (inference)
   float *loss;           // [2]: sum of squared errors, samples
   float nmax;            // plain estimates above this fall back uncorrected
   uint64_t step;
@@ -316,211 +315,130 @@ __device__ __forceinline__ uint32_t pack_rn(float lo, float hi) {
 
 // BF16 copies of W1 (live columns) and W2 from the master, row-major for the
 // training kernel and in mma fragment order for inference.
-__global__ void refresh_bf16_kernel(const float *theta, __nv_bfloat16 *w1c, __nv_bfloat16 *w2) {
+__global__ void refresh_bf16_kernel(const float *theta, __nv_bfloat16 *w1c, __nv_bfloat16 *w2,
+                                    uint2 *w1f, uint2 *w2f) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   for (int i = tid; i < kMlpHid * kMlpLive; i += nth)
     w1c[i] = __float2bfloat16(theta[kOffW1 + (i / kMlpLive) * kMlpIn + w1_col(i % kMlpLive)]);
   for (int i = tid; i < kMlpHid * kMlpHid; i += nth) w2[i] = __float2bfloat16(theta[kOffW2 + i]);
+  // fragment entry e = (kk * 8 + n) * 32 + lane: B[k][j] = W[8n + j][16kk + k]
+  for (int e = tid; e < kW1Frags + kW2Frags; e += nth) {
+    const bool l1 = e < kW1Frags;
+    const int f = l1 ? e : e - kW1Frags;
+    const int lane = f & 31, n = (f >> 5) & 7, kk = f >> 8;
+    const int row = 8 * n + (lane >> 2), k0 = 16 * kk + 2 * (lane & 3);
+    auto W = [&](int k) {
+      return l1 ? theta[kOffW1 + row * kMlpIn + w1_col(k)] : theta[kOffW2 + row * kMlpHid + k];
+    };
+    const uint2 v = make_uint2(pack_rn(W(k0), W(k0 + 1)), pack_rn(W(k0 + 8), W(k0 + 9)));
+    if (l1) w1f[f] = v; else w2f[f] = v;
+  }
 }
-
-// ---------------------------------------------------------------------------
-// Inference on the 5th-generation tensor cores (tcgen05).
-//
-// One CTA of 128 threads handles 128-row tiles of X (persistent, grid-stride);
-// three CTAs share an SM (3 x 128 of its 512 tensor-memory columns).  Per
-// tile:
-//   X tile (128 x 48 BF16) copied in with cp.async one tile ahead, in the
-//   canonical K-major core-matrix layout;
-//   layer 1: D1 = X W1^T (M=128, N=64, K=48: 3 MMAs, accumulator in tensor
-//            memory columns 0..63);
-//   thread r reads row r of D1 (tcgen05.ld), adds b1, applies GELU on BF16
-//   pairs and writes H1 row r (canonical layout) to shared memory;
-//   layer 2: D2 = H1 W2^T (K=64: 4 MMAs, columns 64..127);
-//   thread r: delta = sum_j GELU(D2[r][j] + b2[j]) w3[j] + b3 in FP32.
-// Thread 0 issues the MMAs; tcgen05.commit signals an mbarrier that the
-// others wait on (bounded: a wait longer than 0.2 s sets the error word and
-// the CTA writes NaN for the tile and stops).
-constexpr int kTcRows = 128;
-constexpr int kTcThreads = 128;
-constexpr int kTcCtasPerSm = 3;
-constexpr uint32_t kTcCols = 128;  // tensor-memory columns per CTA: D1 | D2
-constexpr uint64_t kTcWaitNs = 200000000ull;
-
-// Operands need 16-byte alignment (no swizzle).
-struct TcSmem {
-  alignas(16) unsigned char x[2][kTcRows * kMlpLive * 2];  // A of layer 1, double-buffered
-  alignas(16) unsigned char h1[kTcRows * kMlpHid * 2];     // A of layer 2
-  alignas(16) unsigned char w1[kMlpHid * kMlpLive * 2];    // B of layer 1
-  alignas(16) unsigned char w2[kMlpHid * kMlpHid * 2];     // B of layer 2
-  float b1[kMlpHid], b2[kMlpHid], w3[kMlpHid];
-  float b3;
-  uint64_t mbar;
-  uint32_t tmem;
-  int bad;
-};
 
 // 16-byte asynchronous copy global -> shared (zero-filled when src_bytes = 0).
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc_smem_addr(dst)), "l"(src),
-               "r"(src_bytes)
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes)
                : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Rows [r0, r0 + 128) of X into a canonical tile (rows past n: zero).
-__device__ __forceinline__ void tc_load_x(unsigned char *dst, const __nv_bfloat16 *X, uint64_t n,
-                                          uint64_t r0) {
-  for (int i = threadIdx.x; i < kTcRows * (kMlpLive / 8); i += kTcThreads) {
-    const int r = i / (kMlpLive / 8), c = i % (kMlpLive / 8);
+// Start copying rows [r0, r0 + 32) of X into a padded tile (rows past n: 0).
+__device__ __forceinline__ void prefetch_rows(const __nv_bfloat16 *X, uint64_t n, uint64_t r0,
+                                              __nv_bfloat16 *xs) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < 32 * (kMlpLive / 8); i += 32) {
+    const int r = i / (kMlpLive / 8), q = i % (kMlpLive / 8);
     const bool ok = r0 + r < n;
-    cp_async16(dst + tc_canon_off(r, 8 * c, kMlpLive),
-               ok ? (const void *)(X + (r0 + r) * kMlpLive + 8 * c) : (const void *)X, ok ? 16u : 0u);
+    cp_async16(xs + r * kXLd + 8 * q, ok ? (const void *)(X + (r0 + r) * kMlpLive + 8 * q)
+                                          : (const void *)X, ok ? 16u : 0u);
   }
-  asm volatile("cp.async.commit_group;" ::: "memory");
+  cp_async_commit();
 }
 
-template <bool CORRECT>
-__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
-    mlp_tc_kernel(const __nv_bfloat16 *__restrict__ X, uint64_t n, MlpDevWeights w, float nmax,
-                  float *__restrict__ est) {
-  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
-  TcSmem &S = *reinterpret_cast<TcSmem *>(tc_smem_raw);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // weights into the canonical layout, 16 bytes at a time
-  for (int i = tid; i < kMlpHid * (kMlpLive / 8); i += kTcThreads) {
-    const int r = i / (kMlpLive / 8), c = i % (kMlpLive / 8);
-    *reinterpret_cast<uint4 *>(S.w1 + tc_canon_off(r, 8 * c, kMlpLive)) =
-        *reinterpret_cast<const uint4 *>(w.w1c + r * kMlpLive + 8 * c);
+template <int WARPS>
+__device__ __forceinline__ MlpDevWeights stage_weights(const MlpDevWeights &w, uint2 *w1s,
+                                                       uint2 *w2s, float *bs) {
+  for (int i = threadIdx.x; i < kW1Frags; i += WARPS * 32) w1s[i] = w.w1f[i];
+  for (int i = threadIdx.x; i < kW2Frags; i += WARPS * 32) w2s[i] = w.w2f[i];
+  for (int i = threadIdx.x; i < kMlpHid; i += WARPS * 32) {
+    bs[i] = w.b1[i];
+    bs[kMlpHid + i] = w.b2[i];
+    bs[2 * kMlpHid + i] = w.w3[i];
   }
-  for (int i = tid; i < kMlpHid * (kMlpHid / 8); i += kTcThreads) {
-    const int r = i / (kMlpHid / 8), c = i % (kMlpHid / 8);
-    *reinterpret_cast<uint4 *>(S.w2 + tc_canon_off(r, 8 * c, kMlpHid)) =
-        *reinterpret_cast<const uint4 *>(w.w2 + r * kMlpHid + 8 * c);
-  }
-  for (int i = tid; i < kMlpHid; i += kTcThreads) {
-    S.b1[i] = w.b1[i];
-    S.b2[i] = w.b2[i];
-    S.w3[i] = w.w3[i];
-  }
-  if (tid == 0) {
-    S.b3 = *w.b3;
-    S.bad = 0;
-    tc_mbar_init(&S.mbar, 1);
-  }
-  if (warp == 0) tc_alloc<kTcCols>(&S.tmem);
-  tc_fence_before();
+  if (threadIdx.x == 0) bs[3 * kMlpHid] = *w.b3;
   __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = S.tmem;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's tensor-memory lanes
-  constexpr uint32_t idesc = tc_idesc_bf16(kTcRows, kMlpHid);
-  const uint64_t step = (uint64_t)gridDim.x * kTcRows;
-  uint64_t r0 = (uint64_t)blockIdx.x * kTcRows;
+  return MlpDevWeights{w1s, w2s, bs, bs + kMlpHid, bs + 2 * kMlpHid, bs + 3 * kMlpHid};
+}
+
+constexpr int kFwdWarps = 8;
+
+// Shared memory of the forward / correction kernels (dynamic, > 48 KB).
+struct FwdSmem {
+  uint2 w1s[kW1Frags];
+  uint2 w2s[kW2Frags];
+  float bs[3 * kMlpHid + 4];
+  __nv_bfloat16 xs[kFwdWarps][2][32 * kXLd];  // double-buffered input rows
+  __nv_bfloat16 h1s[kFwdWarps][16 * kHLd];     // one tile's hidden layer
+};
+
+// One warp per 32 rows (grid-stride); the next task's rows are copied in
+// while the current ones run through the network.  CORRECT: est (the plain
+// estimates) is replaced by the corrected estimate unless above nmax;
+// otherwise delta is written to est.
+template <bool CORRECT>
+__global__ void __launch_bounds__(kFwdWarps * 32)
+    mlp_rows_kernel(const __nv_bfloat16 *__restrict__ X, uint64_t n, MlpDevWeights w, float nmax,
+                    float *__restrict__ est) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FwdSmem &S = *reinterpret_cast<FwdSmem *>(smem_raw);
+  const MlpDevWeights ws = stage_weights<kFwdWarps>(w, S.w1s, S.w2s, S.bs);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t step = (uint64_t)gridDim.x * kFwdWarps * 32;
+  uint64_t r0 = ((uint64_t)blockIdx.x * kFwdWarps + warp) * 32;
   int buf = 0;
-  if (r0 < n) tc_load_x(S.x[0], X, n, r0);
+  if (r0 < n) prefetch_rows(X, n, r0, S.xs[warp][0]);
   for (; r0 < n; r0 += step, buf ^= 1) {
     if (r0 + step < n) {
-      tc_load_x(S.x[buf ^ 1], X, n, r0 + step);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      prefetch_rows(X, n, r0 + step, S.xs[warp][buf ^ 1]);
+      cp_async_wait<1>();
     } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      cp_async_wait<0>();
     }
-    tc_fence_proxy_async();
-    __syncthreads();
-    // layer 1
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t xa = tc_smem_addr(S.x[buf]), wa = tc_smem_addr(S.w1);
-#pragma unroll
-      for (int ks = 0; ks < kMlpLive / 16; ++ks)
-        tc_mma_bf16(tmem, tc_desc(xa + 256 * ks, 128, kMlpLive * 16),
-                    tc_desc(wa + 256 * ks, 128, kMlpLive * 16), idesc, ks > 0);
-      tc_commit(&S.mbar);
-    }
-    bool ok = tc_mbar_wait(&S.mbar, 0, kTcWaitNs);
-    tc_fence_after();
-    if (ok) {
-      float v[64];
-      tc_ld_x64(tmem + lane_base, v);
-#pragma unroll
-      for (int c = 0; c < kMlpHid / 8; ++c) {
-        uint32_t q[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int k = 8 * c + 2 * j;
-          const __nv_bfloat162 z = __floats2bfloat162_rn(v[k] + S.b1[k], v[k + 1] + S.b1[k + 1]);
-          const __nv_bfloat162 h = gelu_bf16x2(z);
-          q[j] = *reinterpret_cast<const uint32_t *>(&h);
-        }
-        *reinterpret_cast<uint4 *>(S.h1 + tc_canon_off(tid, 8 * c, kMlpHid)) =
-            make_uint4(q[0], q[1], q[2], q[3]);
-      }
-    } else {
-      S.bad = 1;
-    }
-    tc_fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    // layer 2
-    if (tid == 0 && !S.bad) {
-      tc_fence_after();
-      const uint32_t ha = tc_smem_addr(S.h1), wa = tc_smem_addr(S.w2);
-#pragma unroll
-      for (int ks = 0; ks < kMlpHid / 16; ++ks)
-        tc_mma_bf16(tmem + kMlpHid, tc_desc(ha + 256 * ks, 128, kMlpHid * 16),
-                    tc_desc(wa + 256 * ks, 128, kMlpHid * 16), idesc, ks > 0);
-      tc_commit(&S.mbar);
-    }
-    ok = !S.bad && tc_mbar_wait(&S.mbar, 1, kTcWaitNs);
-    tc_fence_after();
-    float d = __int_as_float(0x7fc00000);  // NaN unless the tile completes
-    if (ok) {
-      float v[64];
-      tc_ld_x64(tmem + lane_base + kMlpHid, v);
-      d = S.b3;
-#pragma unroll
-      for (int j = 0; j < kMlpHid; ++j) d += gelu_f(v[j] + S.b2[j]) * S.w3[j];
-    }
-    const uint64_t row = r0 + tid;
-    if (row < n) {
+    __syncwarp();
+    const float d = mlp_forward_warp(S.xs[warp][buf], S.h1s[warp], ws);
+    if (r0 + lane < n) {
       if constexpr (CORRECT) {
-        const float plain = est[row];
+        const float plain = est[r0 + lane];
         float corr = expm1f(log1pf(plain) + d);
         if (!(corr > 0.f)) corr = 0.f;
-        est[row] = plain > nmax ? plain : (ok ? corr : d);
+        est[r0 + lane] = plain > nmax ? plain : corr;
       } else {
-        est[row] = d;
+        est[r0 + lane] = d;
       }
     }
-    tc_fence_before();
-    __syncthreads();  // tensor memory and the tiles are free for the next tile
-    if (S.bad) {
-      if (tid == 0) atomicOr(w.err, 1u);
-      break;
-    }
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tc_dealloc<kTcCols>(tmem);
+    __syncwarp();  // the buffer is refilled two tasks later
   }
 }
 
 template <bool CORRECT>
 cudaError_t launch_mlp_rows(const __nv_bfloat16 *X, uint64_t n, MlpDevWeights w, float nmax,
                             float *est, cudaStream_t st) {
-  const int smem = (int)sizeof(TcSmem);
-  cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<CORRECT>,
+  const int smem = (int)sizeof(FwdSmem);
+  cudaError_t e = cudaFuncSetAttribute(mlp_rows_kernel<CORRECT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
+  int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t tiles = (n + kTcRows - 1) / kTcRows;
-  uint64_t grid = (uint64_t)sms * kTcCtasPerSm;  // persistent: at most 3 CTAs (384 columns) per SM
-  if (tiles < grid) grid = tiles;
-  mlp_tc_kernel<CORRECT><<<(unsigned)grid, kTcThreads, smem, st>>>(X, n, w, nmax, est);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_rows_kernel<CORRECT>, kFwdWarps * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t tasks = (n + 31) / 32;
+  uint64_t grid = (tasks + kFwdWarps - 1) / kFwdWarps;
+  if (grid > (uint64_t)sms * per_sm) grid = (uint64_t)sms * per_sm;  // persistent wave
+  mlp_rows_kernel<CORRECT><<<(unsigned)grid, kFwdWarps * 32, smem, st>>>(X, n, w, nmax, est);
   return cudaGetLastError();
 }
 
@@ -562,8 +480,8 @@ int vbdr_mlp_create(uint64_t seed, vbdr_mlp_t *out) {
   if (e == cudaSuccess) e = cudaMalloc(&m->w1c, kMlpHid * kMlpLive * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->w2, kMlpHid * kMlpHid * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->loss, 2 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(unsigned int));
-  if (e == cudaSuccess) e = cudaMemset(m->err, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&m->w1f, kW1Frags * sizeof(uint2));
+  if (e == cudaSuccess) e = cudaMalloc(&m->w2f, kW2Frags * sizeof(uint2));
   if (e != cudaSuccess) {
     cudaGetLastError();
     vbdr_mlp_destroy(m);
@@ -605,7 +523,8 @@ int vbdr_mlp_destroy(vbdr_mlp_t m) {
   cudaFree(m->w1c);
   cudaFree(m->w2);
   cudaFree(m->loss);
-  cudaFree(m->err);
+  cudaFree(m->w1f);
+  cudaFree(m->w2f);
   delete m;
   return VBDR_OK;
 }
@@ -618,7 +537,7 @@ int vbdr_mlp_set_params(vbdr_mlp_t m, const float *h_params, float nmax) {
   if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, kMlpParams * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, kMlpParams * sizeof(float));
   if (e == cudaSuccess) {
-    refresh_bf16_kernel<<<64, 256>>>(m->theta, m->w1c, m->w2);
+    refresh_bf16_kernel<<<64, 256>>>(m->theta, m->w1c, m->w2, m->w1f, m->w2f);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -694,7 +613,7 @@ int vbdr_mlp_train(vbdr_mlp_t m, const uint16_t *d_X, const float *d_y, uint64_t
                                        weight_decay, b1, b2, eps, bc1, bc2);
       e = cudaGetLastError();
       if (e == cudaSuccess) {
-        refresh_bf16_kernel<<<16, 256, 0, st>>>(m->theta, m->w1c, m->w2);
+        refresh_bf16_kernel<<<16, 256, 0, st>>>(m->theta, m->w1c, m->w2, m->w1f, m->w2f);
         e = cudaGetLastError();
       }
     }
@@ -727,8 +646,8 @@ cudaError_t launch_mlp_correct(const vbdr_mlp *m, const __nv_bfloat16 *X, uint64
 }
 
 MlpDevWeights mlp_weights(const vbdr_mlp *m) {
-  return MlpDevWeights{m->w1c, m->w2, m->theta + kOffB1, m->theta + kOffB2, m->theta + kOffW3,
-                       m->theta + kOffB3, m->err};
+  return MlpDevWeights{m->w1f, m->w2f, m->theta + kOffB1, m->theta + kOffB2, m->theta + kOffW3,
+                       m->theta + kOffB3};
 }
 float mlp_nmax(const vbdr_mlp *m) { return m->nmax; }
 }  // namespace vbk

@@ -12,10 +12,9 @@
 // zero columns of W1 -- the same arithmetic as the full 80-input product.
 //
 // Arithmetic: BF16 inputs, weights and hidden activations fed to the tensor
-// cores (FP32 accumulate); biases, GELU, the output layer and all gradients
-// in FP32.  Inference runs on tcgen05 (128-row tiles, accumulators in tensor
-// memory); training uses warp-level mma.sync.m16n8k16 tiles, whose 64-wide
-// matrices fit a warp exactly.
+// cores with mma.sync.m16n8k16 (FP32 accumulate); biases, GELU, the output
+// layer and all gradients in FP32.  The matrices are 64 wide, so a warp-level
+// m16n8k16 tile fits them exactly.
 #pragma once
 
 #include <cstdint>
@@ -39,14 +38,22 @@ constexpr int kMlpParams = kOffB3 + 1;
 // Column of W1 (80-input layout) holding live input k (0..47).
 __host__ __device__ __forceinline__ int w1_col(int k) { return k < 32 ? k : k + 32; }
 
-// Inference weights: BF16 W1 (live columns) and W2, row-major [64][48] and
-// [64][64] (row = hidden unit, so each is the K-major B operand of its
-// layer), FP32 biases and output weights, and a device error word.
+// BF16 weights in mma fragment order: for k-step kk and 8-column tile n, lane
+// L's B fragment of W^T (two 32-bit words) is w1f[(kk * 8 + n) * 32 + L], so
+// a warp reads a whole fragment with one conflict-free 8-byte load per lane.
+//   layer 1: B[k][j] = W1[8n + j][w1_col(16kk + k)],  kk < 3
+//   layer 2: B[k][j] = W2[8n + j][16kk + k],          kk < 4
+constexpr int kW1Frags = (kMlpLive / 16) * 8 * 32;  // uint2 entries
+constexpr int kW2Frags = (kMlpHid / 16) * 8 * 32;
 struct MlpDevWeights {
-  const __nv_bfloat16 *w1c, *w2;
-  const float *b1, *b2, *w3, *b3;
-  unsigned int *err;
+  const uint2 *w1f;
+  const uint2 *w2f;
+  const float *b1, *b2, *w3, *b3;  // FP32 (global, or staged in shared memory)
 };
+// Padded row strides (elements) of the per-warp input and hidden tiles: 56 and
+// 72 BF16 (28 and 36 words) put the 8 rows of a fragment in distinct banks.
+constexpr int kXLd = 56;
+constexpr int kHLd = 72;
 
 // GELU in its tanh form, z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))),
 // with the hardware tanh approximation (tanh.approx.f32).
@@ -117,6 +124,102 @@ __device__ __forceinline__ void load_b(uint32_t (&b)[2], BT bt) {
   const int lane = threadIdx.x & 31, g = lane >> 2, c = (lane & 3) * 2;
   b[0] = pack_bf16(bt(c, g), bt(c + 1, g));
   b[1] = pack_bf16(bt(c + 8, g), bt(c + 9, g));
+}
+
+// A fragment of a row-major BF16 tile (leading dimension ld elements) whose
+// top-left corner is t: pairs of consecutive columns read as 32-bit words.
+__device__ __forceinline__ void load_a_tile(uint32_t (&a)[4], const __nv_bfloat16 *t, int ld) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, c = (lane & 3) * 2;
+  a[0] = *reinterpret_cast<const uint32_t *>(t + g * ld + c);
+  a[1] = *reinterpret_cast<const uint32_t *>(t + (g + 8) * ld + c);
+  a[2] = *reinterpret_cast<const uint32_t *>(t + g * ld + c + 8);
+  a[3] = *reinterpret_cast<const uint32_t *>(t + (g + 8) * ld + c + 8);
+}
+
+// Forward of 32 rows by one warp, one 16-row tile at a time (32 FP32
+// accumulators live instead of 64, for occupancy).  xs: the rows' live
+// inputs, BF16 [32][kXLd] (first kMlpLive columns used); h1s: scratch BF16
+// [16][kHLd] (one tile's hidden layer).  Returns delta of row (lane) in every
+// lane.
+__device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
+                                                  __nv_bfloat16 *h1s,
+                                                  const MlpDevWeights &w) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, c = (lane & 3) * 2;
+  float part[2][2];  // [tile][row g / g+8]
+#pragma unroll 1
+  for (int m = 0; m < 2; ++m) {
+    float acc[8][4];
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[n][q] = 0.f;
+    // layer 1: [16 x 48] x [48 x 64]
+#pragma unroll
+    for (int kk = 0; kk < kMlpLive / 16; ++kk) {
+      uint32_t a[4];
+      load_a_tile(a, xs + 16 * m * kXLd + 16 * kk, kXLd);
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const uint2 f = w.w1f[(kk * 8 + n) * 32 + lane];
+        const uint32_t b[2] = {f.x, f.y};
+        mma_bf16(acc[n], a, b);
+      }
+    }
+    // bias + GELU -> h1 (BF16; its GELU runs on packed BF16 pairs)
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = g + 8 * h, j = 8 * n + c;
+        const __nv_bfloat162 z = __floats2bfloat162_rn(acc[n][2 * h] + w.b1[j],
+                                                       acc[n][2 * h + 1] + w.b1[j + 1]);
+        *reinterpret_cast<__nv_bfloat162 *>(h1s + r * kHLd + j) = gelu_bf16x2(z);
+      }
+    __syncwarp();
+    // layer 2: [16 x 64] x [64 x 64]
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[n][q] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < kMlpHid / 16; ++kk) {
+      uint32_t a[4];
+      load_a_tile(a, h1s + 16 * kk, kHLd);
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const uint2 f = w.w2f[(kk * 8 + n) * 32 + lane];
+        const uint32_t b[2] = {f.x, f.y};
+        mma_bf16(acc[n], a, b);
+      }
+    }
+    __syncwarp();  // h1s is rewritten by the next tile
+    // output layer in FP32: delta_r = sum_j GELU(z2[r][j]) w3[j] + b3
+    part[m][0] = part[m][1] = 0.f;
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = 8 * n + c + (q & 1);
+        part[m][q >> 1] += gelu_f(acc[n][q] + w.b2[j]) * w.w3[j];
+      }
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      part[m][h] += __shfl_xor_sync(0xffffffffu, part[m][h], 1);
+      part[m][h] += __shfl_xor_sync(0xffffffffu, part[m][h], 2);
+    }
+  // row r lives in lanes 4*(r % 8) .. +3: tile r / 16, half (r / 8) % 2
+  const int src = 4 * (lane & 7);
+  const float d0 = __shfl_sync(0xffffffffu, part[0][0], src);
+  const float d1 = __shfl_sync(0xffffffffu, part[0][1], src);
+  const float d2 = __shfl_sync(0xffffffffu, part[1][0], src);
+  const float d3 = __shfl_sync(0xffffffffu, part[1][1], src);
+  const int slot = lane >> 3;
+  const float delta = slot == 0 ? d0 : slot == 1 ? d1 : slot == 2 ? d2 : d3;
+  __syncwarp();
+  return delta + *w.b3;
 }
 
 }  // namespace vbk

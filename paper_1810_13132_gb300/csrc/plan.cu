@@ -31,7 +31,7 @@
 // expires sets the plan's error word, the producer first waits (bounded) for
 // its copies in flight, and the block's outputs are written as NaN.
 #include "vbdr_internal.cuh"
-#include "tc_sm100.cuh"
+#include "async_sm100.cuh"
 
 namespace vbk {
 namespace {

@@ -1,12 +1,12 @@
 // selftest.cu -- failure detection of the device-side waits.
 //
-// The planned estimate and the MLP kernels wait on mbarriers (TMA copies,
-// tensor-core completions) with a bounded wait: a wait that outlasts its
+// The planned estimate waits on mbarriers (the TMA copies of its ring and
+// the consumers' releases) with a bounded wait: a wait that outlasts its
 // limit returns false, the kernel records the failure in an error word and
 // finishes.  This entry point exercises that path on the GPU without a
 // fault: one warp waits on an mbarrier that nothing ever arrives on.
 #include "../../include/vbdr.h"
-#include "tc_sm100.cuh"
+#include "async_sm100.cuh"
 #include "vbdr_internal.cuh"
 
 namespace vbk {
