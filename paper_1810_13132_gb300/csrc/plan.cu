@@ -46,7 +46,7 @@ constexpr uint32_t kChunkBytes = (uint32_t)kPlanChunk;
 // Every mbarrier wait gives up after this long (a wait that long is a failure).
 constexpr uint64_t kPlanWaitNs = 200000000ull;
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-  return tc_mbar_wait(b, parity, kPlanWaitNs);
+  return mbar_wait_bounded(b, parity, kPlanWaitNs);
 }
 
 __device__ __forceinline__ uint4 ld_stream(const uint4 *p) {
@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     S.acc[0][i] = S.acc[1][i] = S.acc[2][i] = 0;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kPlanSlots; ++i) {
-      tc_mbar_init(&S.full[i], 1);
-      tc_mbar_init(&S.empty[i], kConsumerWarps);
+      mbar_init(&S.full[i], 1);
+      mbar_init(&S.empty[i], kConsumerWarps);
     }
     S.nZZ = pool_noise(d, s, c);
     S.bad = 0;
@@ -178,9 +178,9 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
         }
         const unsigned long long ne = goff[ch + 1] - goff[ch];
         const uint32_t ebytes = 4u * (uint32_t)(ne < kEntCap ? ne : kEntCap);
-        tc_mbar_expect_tx(&S.full[slot], kChunkBytes + ebytes);
-        tc_bulk_load(S.ring[slot], s.reg + (uint64_t)ch * kChunkBytes, kChunkBytes, &S.full[slot]);
-        if (ebytes) tc_bulk_load(S.ents[slot], p.entries + goff[ch], ebytes, &S.full[slot]);
+        mbar_expect_tx(&S.full[slot], kChunkBytes + ebytes);
+        bulk_load_g2s(S.ring[slot], s.reg + (uint64_t)ch * kChunkBytes, kChunkBytes, &S.full[slot]);
+        if (ebytes) bulk_load_g2s(S.ents[slot], p.entries + goff[ch], ebytes, &S.full[slot]);
         issued = ch + 1;
       }
       // every issued copy lands before the block may finish
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
         take(ring, acc, e.w, s.check);
       }
       __syncwarp();
-      if (lane == 0) tc_mbar_arrive(&S.empty[slot]);
+      if (lane == 0) mbar_arrive(&S.empty[slot]);
     }
   }
   __syncthreads();

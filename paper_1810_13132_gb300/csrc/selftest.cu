@@ -14,9 +14,9 @@ namespace {
 
 __global__ void bounded_wait_probe_kernel(uint64_t limit_ns, unsigned int *timed_out) {
   __shared__ uint64_t mbar;
-  if (threadIdx.x == 0) tc_mbar_init(&mbar, 1);
+  if (threadIdx.x == 0) mbar_init(&mbar, 1);
   __syncthreads();
-  if (!tc_mbar_wait(&mbar, 0, limit_ns)) atomicAdd(timed_out, 1u);
+  if (!mbar_wait_bounded(&mbar, 0, limit_ns)) atomicAdd(timed_out, 1u);
 }
 
 }  // namespace
