@@ -239,7 +239,6 @@ constexpr int kPlanChunkLog2 = 15;
 constexpr uint64_t kPlanChunk = 1ull << kPlanChunkLog2;
 constexpr uint32_t kPlanMaxHB = 7000;       // hosts per block (shared accumulators)
 constexpr uint32_t kPlanMaxChunks = 8192;   // Z <= 2^28
-constexpr uint32_t kPlanSentinel = 0xffffffffu;         // no entry (never stored)
 constexpr uint32_t kPlanPad = kPlanMaxHB << kPlanChunkLog2;  // padding: spare host slot
 // Device view of a plan: hosts [blk HB, (blk + 1) HB) form block blk; the
 // entries of group (blk, c) -- one per virtual register of the block's hosts
