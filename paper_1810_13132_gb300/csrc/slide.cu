@@ -33,7 +33,6 @@ template <int W>
 struct Fields {
   static constexpr uint32_t F = 32 / W;               // fields per word
   static constexpr uint32_t FM = (1u << W) - 1u;      // one field
-  static constexpr uint32_t PMAX = (31 + F - 1) / F;  // planes for R <= 31
   static constexpr uint32_t lsb(uint32_t parity) {    // LSB of fields f%2==parity
     uint32_t m = 0;
     for (uint32_t f = parity; f < F; f += 2) m |= 1u << (f * W);
