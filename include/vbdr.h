@@ -409,13 +409,15 @@ VBDR_API int vbdr_server_in_use(vbdr_server_t s, uint64_t *bytes, uint32_t *tena
 
 /* ---- checkpoint / resume ----
  * The complete state of a handle -- configuration, DRV, the slice state
- * (bsLBP1 / nowLBP1 of the current, unclosed slice), registers and pool
- * sums of the last slide -- as one host buffer: a 72-byte header ("VBDRCKP1",
- * configuration, buffer sizes) followed by the raw device buffers.  A handle
- * created with the same configuration that loads it continues exactly as the
- * saved one would have (bit for bit).  Both calls synchronise the stream.
+ * (bsLBP1 / nowLBP1 of the current, unclosed slice), registers, PCSA
+ * statistics (gsmall) and all pool sums of the last slide -- as one host
+ * buffer: an 80-byte header ("VBDRCKP2", configuration, buffer sizes)
+ * followed by the raw device buffers.  A handle created with the same
+ * configuration that loads it continues exactly as the saved one would have
+ * (bit for bit).  Both calls synchronise the stream.
  * save: VBDR_ERANGE if cap < vbdr_state_bytes.  load: VBDR_EINVAL if the
- * buffer is short or was saved with another configuration. */
+ * buffer is short, was saved with another configuration or by another
+ * format version. */
 VBDR_API int vbdr_state_bytes(vbdr_t h, uint64_t *bytes);
 VBDR_API int vbdr_save(vbdr_t h, void *h_buf, uint64_t cap, void *stream);
 VBDR_API int vbdr_load(vbdr_t h, const void *h_buf, uint64_t len, void *stream);
