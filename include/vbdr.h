@@ -85,7 +85,8 @@ typedef struct {
   uint32_t layout;     /* vbdr_layout                                       */
   uint32_t reserved;   /* must be 0                                         */
   uint64_t num_bdr;    /* Z, physical BDRs; must exceed the largest g,
-                          at most 2^32                                      */
+                          at most 2^32 - 1 (the exact pool sum
+                          sum_j 2^(32 - reg_j) <= Z 2^32 must fit 64 bits) */
   uint64_t seed;       /* hash seed A0 (Sec. 4.1); A1 is derived from it    */
 } vbdr_config;
 
@@ -234,7 +235,8 @@ VBDR_API int vbdr_estimate_planned_host(vbdr_t h, vbdr_plan_t p, float *h_out, v
  * or a latency-critical loop that forbids allocation once it runs -- and so
  * cannot create a handle.
  * d_reg: num_bdr uint8 registers (one per physical BDR, as written by
- * vbdr_slide: the largest active LBP1, 0 if none); log2_g: b of every host,
+ * vbdr_slide: the largest active LBP1, 0 if none; a value above 32 is read
+ * as 32); log2_g: b of every host,
  * 1..9; seed: the A0 the registers were built with; d_aips / d_out: as in
  * vbdr_estimate.  The result equals vbdr_estimate on a handle whose registers
  * are d_reg (same FP64 formula, rounded to FP32).
@@ -246,10 +248,13 @@ VBDR_API int vbdr_estimate_planned_host(vbdr_t h, vbdr_plan_t p, float *h_out, v
  * stream capture.  Each call rebuilds the tables for its seed and clears the
  * accumulators; all calls share the one array, so calls whose work overlaps
  * on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.  No cudaMalloc, cudaFree or allocating library
- * routine is called.
+ * serialised by the caller.  The cached address belongs to the CUDA context
+ * it was looked up in: after cudaDeviceReset on that device the library's
+ * module is loaded again elsewhere and the cached address is stale, so do
+ * not call this function after a device reset in the same process.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.
  * Errors: VBDR_ERANGE (log2_g > 9), VBDR_EINVAL (NULL or misaligned pointer,
- * log2_g < 1, num_bdr not in (2^log2_g, 2^32]), VBDR_ECUDA. */
+ * log2_g < 1, num_bdr not in (2^log2_g, 2^32 - 1]), VBDR_ECUDA. */
 VBDR_API int vbdr_estimate_registers_noalloc(const uint8_t *d_reg, uint64_t num_bdr,
                                              uint32_t log2_g, uint64_t seed,
                                              const uint32_t *d_aips, uint64_t n_hosts,
@@ -338,15 +343,19 @@ VBDR_API int vbdr_mlp_forward(vbdr_mlp_t m, const uint16_t *d_X, uint64_t n, flo
                               void *stream);
 
 /* Feature rows of n hosts from the handle's registers (d_X BF16 [n][48],
- * device) and their plain estimates (d_plain FP32 [n], device, may be NULL).
- * Errors: as vbdr_estimate. */
+ * device, 16-byte aligned) and their plain estimates (d_plain FP32 [n],
+ * device, may be NULL).  The histogram bins count in 16-bit fields, so every
+ * host's g must be at most 512 (the learned correction is trained on
+ * g = 256).  Errors: as vbdr_estimate, plus VBDR_ERANGE (largest g of the
+ * handle above 512) and VBDR_EINVAL (d_X not 16-byte aligned). */
 VBDR_API int vbdr_features(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts, uint16_t *d_X,
                            float *d_plain, void *stream);
 
 /* vbdr_estimate with the learned correction fused into the same kernel:
  * the gather also builds each host's register histogram, the MLP runs on the
  * tensor cores per batch of 32 hosts, and d_out receives the corrected
- * estimate (the plain one where n_plain > nmax).  Errors: as vbdr_estimate. */
+ * estimate (the plain one where n_plain > nmax).  Errors: as vbdr_estimate,
+ * plus VBDR_ERANGE (largest g of the handle above 512, as vbdr_features). */
 VBDR_API int vbdr_estimate_learned(vbdr_t h, vbdr_mlp_t m, const uint32_t *d_aips,
                                    uint64_t n_hosts, float *d_out, void *stream);
 

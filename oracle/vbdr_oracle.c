@@ -21,8 +21,8 @@
  *            scanIPpairOnGpu (VBDR-gfast); Alg. 8 BeginSliceUpdateDRV and
  *            Alg. 9 scanIPpairUpdatDRV (VBDR-gsmall); Table 1.
  *
- * Readings of places where the paper is silent or garbled (each one is
- * listed with its reason in the design notes of the repository):
+ * Readings of places where the paper is silent or garbled, each with the
+ * reason it is taken:
  *   H(x,N,A)  : the paper only says "random hash with seed A mapping x into
  *               [0,N)" (Sec. 4.1).  Read as the SplitMix64 finaliser
  *               (Steele, Lea & Flood 2014):
@@ -143,7 +143,8 @@ static uint32_t orc_dr_width(uint32_t k) {
 /* Returns NULL on invalid parameters or allocation failure. */
 orc_t *orc_create(int variant, uint32_t k, uint64_t Z, uint32_t b_default,
                   uint32_t b_min, uint32_t group_rule, uint64_t seed) {
-  if (variant < 0 || variant > 2 || k == 0 || Z == 0 || Z > (1ULL << 32))
+  /* Z < 2^32: the exact pool sum sum_j 2^(32 - reg_j) <= Z 2^32 fits 64 bits */
+  if (variant < 0 || variant > 2 || k == 0 || Z == 0 || Z >= (1ULL << 32))
     return NULL;
   if (group_rule > 1 || b_min < 1 || b_min > 16) return NULL;
   if (group_rule == 0 && (b_default < b_min || b_default > 16)) return NULL;

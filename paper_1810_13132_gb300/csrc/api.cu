@@ -135,6 +135,13 @@ int fail_cuda(vbdr *h, cudaError_t e) {
   return VBDR_OK;
 }
 
+// Largest log2 g of any host of the handle.
+uint32_t max_log2_g(const Dims &d) { return d.group_rule ? d.b_min + 3 : d.b; }
+
+// The feature histogram counts a host's register values in 8-bit fields per
+// lane and 16-bit fields per host: g <= 512 keeps every count in range.
+constexpr uint32_t kMaxFeatureLog2G = 9;
+
 uint32_t ktab_entries(const Dims &d) {
   const uint32_t gmax = 1u << (d.group_rule ? d.b_min + 3 : d.b);
   return gmax > (uint32_t)vbk::kKtabSize ? gmax : (uint32_t)vbk::kKtabSize;
@@ -193,7 +200,8 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
     return VBDR_EINVAL;
   if (cfg->group_rule == 1 && b_min + 3 > 9) return VBDR_EINVAL;
   const uint32_t b_max = cfg->group_rule ? b_min + 3 : cfg->log2_g;
-  if (cfg->num_bdr == 0 || cfg->num_bdr > (1ull << 32) ||
+  // the exact pool sum sum_j 2^(32 - reg_j) <= Z 2^32 must fit 64 bits
+  if (cfg->num_bdr == 0 || cfg->num_bdr >= (1ull << 32) ||
       cfg->num_bdr <= (1ull << b_max))
     return VBDR_EINVAL;
 
@@ -203,7 +211,7 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   Dims &d = h->d;
   d.Z = cfg->num_bdr;
   d.Zs = (d.Z + 3) & ~3ull;
-  d.zmul = d.Z == (1ull << 32) ? 0u : (uint32_t)d.Z;
+  d.zmul = (uint32_t)d.Z;
   d.k = cfg->k;
   d.w = 0;
   while ((1u << d.w) < cfg->k + 1) ++d.w;
@@ -434,7 +442,10 @@ int vbdr_features(vbdr_t h, const uint32_t *d_aips, uint64_t n, uint16_t *d_X, f
   if (h->sticky) return h->sticky;
   if (!h->slid) return VBDR_EORDER;
   if (n == 0) return VBDR_OK;
-  if (!d_aips || !d_X || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_X & 3u)) return VBDR_EINVAL;
+  // feature rows are written with 8- and 16-byte stores
+  if (!d_aips || !d_X || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_X & 15u)) return VBDR_EINVAL;
+  if (d_plain && ((uintptr_t)d_plain & 3u)) return VBDR_EINVAL;
+  if (max_log2_g(h->d) > kMaxFeatureLog2G) return VBDR_ERANGE;
   float *plain = d_plain;
   cudaStream_t st = (cudaStream_t)stream;
   if (!plain) {  // the kernel always writes the plain estimates: use the staging buffer
@@ -455,6 +466,7 @@ int vbdr_estimate_learned(vbdr_t h, vbdr_mlp_t m, const uint32_t *d_aips, uint64
   if (n == 0) return VBDR_OK;
   if (!d_aips || !d_out || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_out & 3u))
     return VBDR_EINVAL;
+  if (max_log2_g(h->d) > kMaxFeatureLog2G) return VBDR_ERANGE;
   cudaStream_t st = (cudaStream_t)stream;
   if (n > h->feat_cap) {
     // feature rows live in a buffer owned by the handle, grown here (never

@@ -113,7 +113,10 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
             const uint32_t pidx = reduce32(hash32(aip, kt[i]), d.zmul);
             if (vbk_check(pidx < d.Z, s.check, kChkPidx)) {
               M[u] = __ldg(vals + pidx);
+              // the checked build skips and records a value above 32; the
+              // plain build reads it as 32 (registers a caller supplies)
               if (!vbk_check(M[u] <= 32u, s.check, kChkReg)) M[u] = 0xffu;
+              else M[u] = min(M[u], 32u);
             }
           }
         }

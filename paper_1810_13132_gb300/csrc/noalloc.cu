@@ -13,7 +13,9 @@
 // each call first rebuilds what it reads (seed table, ln table) and clears
 // the accumulators that must start at zero.  Calls whose work overlaps on the
 // GPU (different streams, or different host threads) race on the array and
-// must be serialised by the caller.
+// must be serialised by the caller.  The cached address belongs to the CUDA
+// context it was resolved in; after cudaDeviceReset it is stale (documented
+// in the header: no call after a device reset in the same process).
 #include <cmath>
 #include <mutex>
 
@@ -67,13 +69,14 @@ __global__ void noalloc_prepare_kernel(NoallocScratch *sc, uint64_t A0, uint32_t
 }
 
 // Pool sums S_Z = sum_j 2^(32 - reg_j), V_Z = #{reg_j = 0} over the caller's
-// registers; the last block publishes them into sums[0], sums[1].
+// registers (values above 32 read as 32, as in the estimate's gather); the
+// last block publishes them into sums[0], sums[1].
 __global__ void __launch_bounds__(256)
     noalloc_pool_sums_kernel(const uint8_t *__restrict__ reg, uint64_t Z, NoallocScratch *sc) {
   unsigned long long S = 0, V = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < Z; j += stride) {
-    const uint32_t M = reg[j];
+    const uint32_t M = min((uint32_t)reg[j], 32u);  // a caller's value above 32 reads as 32
     S += 1ull << (32u - M);
     V += (M == 0u);
   }
@@ -117,7 +120,8 @@ extern "C" int vbdr_estimate_registers_noalloc(const uint8_t *d_reg, uint64_t nu
   using namespace vbk;
   if (log2_g < 1) return VBDR_EINVAL;
   if (log2_g > kNoallocMaxLog2G) return VBDR_ERANGE;
-  if (num_bdr == 0 || num_bdr > (1ull << 32) || num_bdr <= (1ull << log2_g)) return VBDR_EINVAL;
+  // the exact pool sum sum_j 2^(32 - reg_j) <= Z 2^32 must fit 64 bits
+  if (num_bdr == 0 || num_bdr >= (1ull << 32) || num_bdr <= (1ull << log2_g)) return VBDR_EINVAL;
   if (!d_reg) return VBDR_EINVAL;
   if (n_hosts == 0) return VBDR_OK;
   if (!d_aips || !d_out || ((uintptr_t)d_aips & 3u) || ((uintptr_t)d_out & 3u))
@@ -129,7 +133,7 @@ extern "C" int vbdr_estimate_registers_noalloc(const uint8_t *d_reg, uint64_t nu
   Dims d = {};
   d.Z = num_bdr;
   d.Zs = (num_bdr + 3) & ~3ull;
-  d.zmul = num_bdr == (1ull << 32) ? 0u : (uint32_t)num_bdr;
+  d.zmul = (uint32_t)num_bdr;
   d.b = log2_g;
   d.b_min = log2_g;
   d.group_rule = 0;

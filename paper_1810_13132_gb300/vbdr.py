@@ -543,6 +543,16 @@ def estimate_registers_noalloc(reg, num_bdr: int, log2_g: int, seed: int, aips, 
                                stream=None) -> None:
     """vbdr_estimate_registers_noalloc on device tensors: estimates straight
     from a register array, with no device allocation inside the library."""
+    import torch
+    # The C entry point cannot see buffer sizes: check them here, so that a
+    # short tensor is refused instead of being read or written past its end.
+    dev = torch.device("cuda", torch.cuda.current_device())
+    assert reg.is_cuda and reg.device == dev and reg.is_contiguous() and reg.dtype == torch.uint8
+    assert reg.numel() >= num_bdr, "reg holds fewer than num_bdr registers"
+    assert aips.is_cuda and aips.device == dev and aips.is_contiguous()
+    assert aips.dtype in (torch.int32, torch.uint32)
+    assert out.is_cuda and out.device == dev and out.is_contiguous() and out.dtype == torch.float32
+    assert out.numel() >= aips.numel(), "out is shorter than aips"
     L = load()
     n = aips.numel()
     _check("vbdr_estimate_registers_noalloc", L.vbdr_estimate_registers_noalloc(

@@ -52,6 +52,7 @@ def _cfg(**kw):
 @pytest.mark.parametrize("bad", [
     dict(k=0), dict(k=256), dict(layout=3), dict(reserved=1), dict(group_rule=2),
     dict(log2_g=0), dict(log2_g=17), dict(num_bdr=0), dict(num_bdr=(1 << 32) + 1),
+    dict(num_bdr=1 << 32),  # the exact pool sum must fit 64 bits
     dict(num_bdr=128),  # Z must exceed g = 128
     dict(group_rule=1, log2_g_min=7),  # b_min + 3 > 9
     dict(log2_g=5, log2_g_min=6),
@@ -79,6 +80,16 @@ def test_null_handle_calls(lib):
     assert lib.vbdr_plan_status(None) == -1
     assert lib.vbdr_estimate_planned(None, None, None, None) == -1
     assert lib.vbdr_estimate_planned_host(None, None, None, None) == -1
+
+
+def test_noalloc_rejects_invalid_sizes_without_touching_the_gpu(lib):
+    f = lib.vbdr_estimate_registers_noalloc
+    dummy = ctypes.c_void_p(16)  # never dereferenced: the sizes are refused first
+    assert f(dummy, 1 << 32, 8, 1, dummy, 1, dummy, None) == -1  # Z = 2^32
+    assert f(dummy, 256, 8, 1, dummy, 1, dummy, None) == -1      # Z must exceed g
+    assert f(dummy, 1 << 20, 0, 1, dummy, 1, dummy, None) == -1  # log2_g < 1
+    assert f(dummy, 1 << 20, 10, 1, dummy, 1, dummy, None) == -4  # g above 512
+    assert f(None, 1 << 20, 8, 1, dummy, 1, dummy, None) == -1
 
 
 def test_oracle_and_library_share_no_source():

@@ -60,6 +60,13 @@ def _target(n_plain, card):
 
 
 def test_gradient_matches_fp64_reference(data):
+    """Every gradient element against the FP64 reference at the parameters
+    and inputs the GPU reads (BF16 W1, W2 and X).  The GPU stores h1, dZ2 and
+    dZ1 in BF16 (relative rounding 2^-9) and evaluates GELU with the
+    hardware tanh (relative error 2^-11), so each term of a gradient sum
+    carries a relative error of a few 1e-3; the bound per element is
+    2e-2 max(|g_ref|, rms of that layer's gradient), the floor covering
+    elements whose terms cancel."""
     from paper_1810_13132_gb300 import Mlp
     Xtr, ptr, ctr = data[:3]
     X, y = Xtr[:1000], _target(ptr[:1000], ctr[:1000])
@@ -72,14 +79,24 @@ def test_gradient_matches_fp64_reference(data):
     theta = _rounded_reference_params(params)
     g_ref = learned.gradient(theta, Xr, y)
     assert loss_gpu == pytest.approx(learned.loss(theta, Xr, y), rel=2e-2)
-    live = np.ones(learned.N_PARAMS, bool)
-    W1 = np.zeros((64, 80), bool)
-    W1[:, 32:64] = True  # columns of always-zero inputs: no gradient on either side
-    live[:64 * 80] = ~W1.ravel()
-    err = np.linalg.norm(g_gpu[live] - g_ref[live]) / np.linalg.norm(g_ref[live])
-    cos = g_gpu[live] @ g_ref[live] / np.linalg.norm(g_gpu[live]) / np.linalg.norm(g_ref[live])
-    assert err < 3e-2 and cos > 0.999, (err, cos)
-    assert np.abs(g_gpu[~live]).max() == 0.0
+    off = 0
+    for name, shape in learned.SIZES:
+        k = int(np.prod(shape))
+        got, want = g_gpu[off:off + k].astype(np.float64), g_ref[off:off + k]
+        live = np.ones(k, bool)
+        if name == "W1":
+            dead = np.zeros((64, 80), bool)
+            dead[:, 32:64] = True  # columns of always-zero inputs: no gradient on either side
+            live = ~dead.ravel()
+            assert np.abs(got[~live]).max() == 0.0
+        rms = np.sqrt(np.mean(want[live] ** 2))
+        bound = 2e-2 * np.maximum(np.abs(want[live]), rms)
+        ratio = np.abs(got[live] - want[live]) / bound
+        worst = int(np.argmax(ratio))
+        assert ratio.max() <= 1.0, (name, float(ratio.max()), worst, got[live][worst],
+                                    want[live][worst], rms)
+        off += k
+    assert off == learned.N_PARAMS
 
 
 def test_forward_matches_fp64_reference(data):

@@ -491,6 +491,98 @@ def test_invalid_parameters_rejected():
         Oracle("gfast", k=0, Z=100, b=4, seed=1)
     with pytest.raises(ValueError):
         Oracle("gfast", k=3, Z=16, b=4, seed=1)  # Z must exceed g
+    with pytest.raises(ValueError):
+        Oracle("gfast", k=3, Z=1 << 32, b=4, seed=1)  # the pool sum must fit 64 bits
     o = Oracle("gfast", k=3, Z=100, b=4, seed=1)
     with pytest.raises(RuntimeError):
         o.estimate(np.array([1], dtype=np.uint32))
+
+
+# ------------------------------------------ register-level state loading
+
+def _virtual_registers_of(o, reg, aips):
+    """Host-major virtual registers reg[pidx(aip, i)], i < g(aip), with pidx
+    from Alg. 3 (o.phy_idx, pinned above), and their offsets."""
+    gs = [1 << o.host_b(int(a)) for a in aips]
+    offsets = np.concatenate([[0], np.cumsum(gs)[:-1]]).astype(np.uint64)
+    vregs = np.empty(int(sum(gs)), dtype=np.uint8)
+    for h, a in enumerate(aips):
+        for i in range(gs[h]):
+            vregs[int(offsets[h]) + i] = reg[o.phy_idx(int(a), i)]
+    return offsets, vregs
+
+
+def test_load_virtual_registers_rebuilds_scanned_state():
+    """Invariant: after a scan, every physical register is the largest of
+    the virtual registers that Alg. 3 maps onto it (a BDR no pair reached is
+    0).  So loading the virtual registers a scanned state implies, for the
+    hosts that made the traffic, rebuilds that state's registers exactly --
+    into an instance whose registers were dirty before (untouched BDRs must
+    come out 0), with mixed g (host-major offsets of uneven length)."""
+    k, Z, b_min = 3, 1 << 14, 5
+    gen = traffic.ZipfTraffic(60, 1.1, 3000, k, seed=41)
+    o = Oracle("gfast", k=k, Z=Z, b=b_min + 3, seed=SEED, b_min=b_min, group_rule=1)
+    for _ in range(3):
+        o.scan(gen.next_slice(20000))
+        o.slide()
+    reg = o.registers()
+    assert (reg == 0).sum() > Z // 4  # BDRs no host maps to stay 0
+    assert len({o.host_b(int(a)) for a in gen.aips}) >= 3
+    offsets, vregs = _virtual_registers_of(o, reg, gen.aips)
+    dirty = Oracle("gfast", k=k, Z=Z, b=b_min + 3, seed=SEED, b_min=b_min, group_rule=1)
+    other = traffic.ZipfTraffic(2000, 1.1, 3000, k, seed=42)
+    dirty.scan(other.next_slice(60000))
+    dirty.slide()
+    # stale values where the loaded hosts map nothing, and where they do
+    assert ((dirty.registers() != 0) & (reg == 0)).sum() > 1000
+    assert (dirty.registers() != reg).sum() > Z // 4
+    dirty.load_virtual_registers(gen.aips, offsets, vregs)
+    np.testing.assert_array_equal(dirty.registers(), reg)
+    assert dirty.pool_sums() == o.pool_sums()
+    np.testing.assert_allclose(dirty.estimate(gen.aips), o.estimate(gen.aips), rtol=0, atol=0)
+
+
+def test_load_virtual_registers_collisions_fold_by_max():
+    """Brute force on a tiny pool: two hosts whose virtual registers collide
+    on physical BDRs; each physical register is the maximum over its
+    colliding virtual registers, the rest 0."""
+    Z, b = 97, 4
+    o = Oracle("gfast", k=2, Z=Z, b=b, seed=SEED)
+    rng = np.random.default_rng(43)
+    aips = traffic.distinct_u32(rng, 12)
+    vregs = rng.integers(0, 29, size=12 * 16).astype(np.uint8)
+    offsets = (np.arange(12) * 16).astype(np.uint64)
+    want = np.zeros(Z, dtype=np.uint8)
+    hits = np.zeros(Z, dtype=np.int64)
+    for h, a in enumerate(aips):
+        for i in range(16):
+            j = o.phy_idx(int(a), i)
+            hits[j] += 1
+            want[j] = max(want[j], vregs[h * 16 + i])
+    assert (hits >= 2).sum() > 10  # collisions happen
+    o.load_virtual_registers(aips, offsets, vregs)
+    np.testing.assert_array_equal(o.registers(), want)
+    S = sum(1 << (32 - int(m)) for m in want)
+    assert o.pool_sums() == (S, int((want == 0).sum()))
+
+
+def test_load_virtual_registers_accuracy_per_group():
+    """Statistical pin of the register-level workload: registers drawn as
+    the maximum of Poisson(c/g) geometric LBP1 values and loaded into a
+    pool far larger than the load are HyperLogLog registers of c items, so
+    each g group's estimates have relative standard error about 1.04/sqrt(g)
+    (Flajolet et al. 2007) and little bias."""
+    from synth.registers import BatchedRegisters
+    b_min = 6
+    br = BatchedRegisters(1200, b_min, 3e5, seed=44)
+    keep = br.card >= 200  # above HLL's small-range regime
+    o = Oracle("gfast", k=60, Z=1 << 22, b=b_min + 3, seed=SEED, b_min=b_min, group_rule=1)
+    o.load_virtual_registers(br.aips, br.offsets, br.vregs)
+    est = o.estimate(br.aips)
+    for b in range(b_min, b_min + 4):
+        sel = keep & (br.b == b)
+        assert sel.sum() > 100
+        rel = (est[sel] - br.card[sel]) / br.card[sel]
+        sigma = 1.04 / math.sqrt(1 << b)
+        assert math.sqrt(np.mean(rel ** 2)) < 1.5 * sigma, (b, math.sqrt(np.mean(rel ** 2)))
+        assert abs(np.mean(rel)) < 4 * sigma / math.sqrt(sel.sum()) + 0.01, b

@@ -49,6 +49,11 @@ MUTANTS = {
                       "double n = (Z * g / (Z + g)) * (n_g / g - n_Z / Z);"),
     "harmonic_exponent": ("s += 1ULL << (32 - M);", "s += 1ULL << (31 - M);"),
     "dr_width_short": ("while ((1u << w) < k + 1) ++w;", "while ((1u << w) < k) ++w;"),
+    # register-level state loading (batched workload)
+    "load_min_fold": ("      if (v > o->reg[j]) o->reg[j] = v;", "      if (v < o->reg[j]) o->reg[j] = v;"),
+    "load_no_zero_fill": ("  memset(o->reg, 0, (size_t)o->Z);\n  for (uint64_t h = 0; h < n; ++h) {",
+                          "  for (uint64_t h = 0; h < n; ++h) {"),
+    "load_ignores_offsets": ("      uint8_t v = vregs[offsets[h] + i];", "      uint8_t v = vregs[h * g + i];"),
     # LogLog / PCSA (pins in test_oracle_alt.py)
     "loglog_alpha_exponent": ("return pow(base, -m);", "return pow(base, m);"),
     "loglog_mean_not_divided": ("return orc_loglog_alpha(m) * m * exp2((double)L / m);",
