@@ -3,9 +3,15 @@ trace workload (k = 30, 64M (aip, bip) pairs per slice, 1M Zipf(1.05) hosts
 with cardinalities 1..2M, 10% in-slice repeats, Z = 2^24 BDRs, g = 256):
 scan the slice, close it (slide), estimate every host.
 
-Prints one JSON line (see the repository's design notes for every key).
+Prints one JSON line: the contract's keys (metric, value, unit, n_gpus,
+steps, warmup, ms_per_step, ..., e2e, gpu_launches, clocks, roofline,
+cpu_baseline) plus the per-kernel times and rooflines (kernels,
+scan_roofline), the accuracy against exact counts, the learned correction's
+latency, and -- on one GPU -- the same step in the gsmall layout (gsmall),
+the batched 4M-host estimate (batched) and a short two-tenant serving run
+(serve).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--layout gfast|gsmall] [--workload trace|small]
+                  [--layout gfast|gsmall] [--workload trace|small|batched|serve]
 Under torchrun (N > 1) every rank runs an independent replica (its own pool
 and traffic): weak scaling, no collective on the data path.
 """
@@ -49,6 +55,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mre", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="trace: skip the gsmall, batched and serving sections of the line")
     p.add_argument("--pairs", type=int, default=0, help="override pairs per slice (profiling)")
     p.add_argument("--slices", type=int, default=N_DISTINCT_SLICES,
                    help="distinct device-resident slices cycled through")
@@ -373,12 +381,11 @@ def run_ours(a):
     peak, peak_kind = _peaks()
     Z, P = wl["Z"], v.words
     scan_bytes = 8 * N
-    slide_bytes = {"gfast": Z * ((4 * P + 4) + (4 * P + 4 + 1)),   # DRV + bsLBP1 in, DRV + bsLBP1 + reg out
-                   "gsmall": Z * (4 * P + 4 * P + 1 + 1),           # DRV in, DRV + reg + PCSA out
-                   "serial": Z * ((4 * P + 1) + (4 * P + 1 + 1))}[a.layout]  # DRV + nowLBP1
-    est_bytes = H * (4 + 4) + Z
-    if planned:  # the plan is read once per launch: host list, group offsets, entries
-        est_bytes = plan_info["device_bytes"] + 4 * H + Z
+    slide_bytes = _slide_bytes(a.layout, Z, P)
+    # the estimate's algorithmic bytes: host address, group byte and result
+    # per host (4 + 1 + 4) plus one read of the register array; the H g
+    # virtual-register reads are L2 hits of that array, not HBM traffic
+    est_bytes = H * (4 + 1 + 4) + Z
     kern = {"scan": (statistics.mean(scan_ms), scan_bytes),
             "slide": (statistics.mean(slide_ms), slide_bytes),
             "estimate": (statistics.mean(est_ms), est_bytes)}
@@ -393,16 +400,23 @@ def run_ours(a):
         per_kernel[name] = {"ms": round(ms, 4), "algorithmic_bytes": int(nbytes),
                             "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
                             "traffic": _ncu_traffic(tkey.get(name, name), a.layout, a.workload)}
-    limiter = {"estimate": ("shared-memory pipe: one random byte read and one shared atomic per "
-                            "plan entry; DRAM carries the plan stream" if planned else
-                            "L1TEX/L2 rate of random 1-byte register gathers (ncu: L1TEX 96%, L2 73%, "
-                            "99% L2 hits); DRAM carries only hosts and the 16 MiB register array"),
-               "scan": "L2 random-sector rate of the update-word test loads plus the hash arithmetic",
+    limiter = {"estimate": ("shared-memory pipe (one random byte read and one shared atomic per "
+                            "plan entry) and the plan stream: DRAM moves the plan, "
+                            f"{plan_info['device_bytes'] if planned else 0} B per launch, far above "
+                            "the algorithmic bytes" if planned else
+                            "L1TEX/L2 rate of random 1-byte register gathers; DRAM carries only "
+                            "hosts and the register array"),
+               "scan": "L1TEX request rate of the per-pair update-word tests plus the hash arithmetic",
                "slide": "HBM streaming of the DRV planes with the SWAR field arithmetic"}[dom]
+    scan_t = statistics.mean(scan_ms)
+    scan_gbs = scan_bytes / (scan_t * 1e-3) / 1e9
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(wl, gen, slices)
     clocks = clk.summary()
+    extras = {}
+    if rank == 0 and ws == 1 and not a.no_extras and a.workload == "trace":
+        extras = run_extras(a, wl, slices, d_slices, plan, d_aips, peak)
     line = {
         "metric": _metric_name(),
         "value": round(value, 3), "unit": "G pairs/s",
@@ -417,15 +431,24 @@ def run_ours(a):
                    "estimate": ("planned: host-to-register plan of the fixed host list built once "
                                 "before the timed steps" if planned else "gather"),
                    "parallelism": f"replicas x{ws}"},
-        "scan_gpairs_per_s": round(N / (statistics.mean(scan_ms) * 1e-3) / 1e9, 3),
-        "scan_ms": round(statistics.mean(scan_ms), 4),
+        "scan_gpairs_per_s": round(N / (scan_t * 1e-3) / 1e9, 3),
+        "scan_ms": round(scan_t, 4),
         "slide_ms": round(statistics.mean(slide_ms), 4),
         "slide_gbs": round(slide_bytes / (statistics.mean(slide_ms) * 1e-3) / 1e9, 1),
         "estimate_ms": round(statistics.mean(est_ms), 4),
-        "scan_hbm_frac": round(scan_bytes / (statistics.mean(scan_ms) * 1e-3) / 1e9 / peak, 4),
+        "scan_hbm_frac": round(scan_gbs / peak, 4),
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": traffic_bytes, "peak_kind": peak_kind, "limiter": limiter},
+                     "traffic": traffic_bytes, "peak_kind": peak_kind, "limiter": limiter,
+                     "algorithmic_bytes": int(dbytes),
+                     "traffic_over_algorithmic": (round(traffic_bytes / dbytes, 2)
+                                                  if traffic_bytes else None)},
+        "scan_roofline": {"bound": "hbm", "achieved": round(scan_gbs, 1), "peak": peak,
+                          "unit": "GB/s", "frac": round(scan_gbs / peak, 4),
+                          "algorithmic_bytes": scan_bytes,
+                          "traffic": per_kernel["scan"]["traffic"], "peak_kind": peak_kind,
+                          "limiter": ("L1TEX request rate: one random 4-byte test of the "
+                                      "update word per pair")},
         "kernels": per_kernel,
         "plan": plan_info,
         "gather_estimate": gather,
@@ -436,11 +459,80 @@ def run_ours(a):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    line.update(extras)
     if rank == 0:
         print(json.dumps(line), flush=True)
     v.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _slide_bytes(layout, Z, P):
+    """Algorithmic bytes of one slide: every DRV plane word read and written,
+    plus the layout's slice state and the register (and PCSA) bytes."""
+    return {"gfast": Z * ((4 * P + 4) + (4 * P + 4 + 1)),   # DRV + bsLBP1 in, DRV + bsLBP1 + reg out
+            "gsmall": Z * (4 * P + 4 * P + 1 + 1),           # DRV in, DRV + reg + PCSA out
+            "serial": Z * ((4 * P + 1) + (4 * P + 1 + 1))}[layout]  # DRV + nowLBP1
+
+
+def run_extras(a, wl, slices, d_slices, plan, d_aips, peak):
+    """The rest of the hot path's configurations, measured in the same run:
+    the trace step in the gsmall layout, batched estimation of 4M hosts and
+    a short serving run."""
+    out = {}
+    try:
+        out["gsmall"] = _trace_layout_step(a, wl, d_slices, plan, d_aips, "gsmall", peak)
+    except Exception as e:  # reported, never fatal to the main line
+        out["gsmall"] = {"error": repr(e)}
+    try:
+        out["batched"] = batched_core(a)
+    except Exception as e:
+        out["batched"] = {"error": repr(e)}
+    try:
+        out["serve"] = serve_core(a, tenants=2, slices_per_tenant=40, warmup=3)
+    except Exception as e:
+        out["serve"] = {"error": repr(e)}
+    return out
+
+
+def _trace_layout_step(a, wl, d_slices, plan, d_aips, layout, peak):
+    """The trace step (scan + slide + planned estimate) in another layout, on
+    the same device-resident slices and host-list plan, timed per kernel."""
+    import torch
+    from paper_1810_13132_gb300 import Config, Vbdr
+    N, H = wl["n_pairs"], wl["n_hosts"]
+    v = Vbdr(Config(k=wl["k"], num_bdr=wl["Z"], log2_g=wl["log2_g"], layout=layout, seed=SEED))
+    out = torch.empty(H, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    nsl = len(d_slices)
+    for i in range(a.warmup):
+        v.scan(d_slices[i % nsl]); v.slide(); v.estimate_planned(plan, out=out)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(a.steps)]
+    for i in range(a.steps):
+        e = evs[i]
+        e[0].record(stream)
+        v.scan(d_slices[(a.warmup + i) % nsl])
+        e[1].record(stream)
+        v.slide()
+        e[2].record(stream)
+        v.estimate_planned(plan, out=out)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    plan.status()
+    sc = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    sl = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    es = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    tot = evs[0][0].elapsed_time(evs[-1][3]) / a.steps
+    sb = _slide_bytes(layout, wl["Z"], v.words)
+    v.close()
+    return {"layout": layout, "value": round(N / (tot * 1e-3) / 1e9, 3), "unit": "G pairs/s",
+            "ms_per_step": round(tot, 4), "scan_ms": round(sc, 4),
+            "scan_gpairs_per_s": round(N / (sc * 1e-3) / 1e9, 3),
+            "scan_hbm_frac": round(8 * N / (sc * 1e-3) / 1e9 / peak, 4),
+            "slide_ms": round(sl, 4), "slide_gbs": round(sb / (sl * 1e-3) / 1e9, 1),
+            "slide_hbm_frac": round(sb / (sl * 1e-3) / 1e9 / peak, 4),
+            "estimate_ms": round(es, 4), "steps": a.steps, "warmup": a.warmup}
 
 
 def _ncu_traffic(kernel, layout, workload):
@@ -456,11 +548,11 @@ def _ncu_traffic(kernel, layout, workload):
 
 # ------------------------------------------------ batched estimation arm
 
-def run_batched(a):
+def batched_core(a):
     """4M hosts, cardinalities 1..1e7 log-uniform, g in {64,128,256,512}
     mixed by host group, Z = 2^26, k = 60; register-level synthetic state.
     Times one persistent launch (default shape, then the autotuned shape)
-    against one plain launch per g group."""
+    against one plain launch per g group, and the planned estimate."""
     import torch
     from paper_1810_13132_gb300 import Config, Vbdr
     from synth.registers import BatchedRegisters
@@ -512,14 +604,12 @@ def run_batched(a):
     plan.status()
     planned_same = bool(torch.equal(out_p.view(torch.int32), out.view(torch.int32)))
     plan.close()
-    line = {
-        "metric": "batched estimate: hosts/s (one persistent autotuned launch)",
+    v.close()
+    load = float(br.card.sum()) / Z
+    return {
+        "workload": "batched 4M hosts c~logU(1,1e7) g in {64..512} Z=2^26 k=60",
+        "hosts": H, "Z": Z, "k": k, "virtual_registers": gathers,
         "value": round(H / (tuned_ms * 1e-3) / 1e6, 2), "unit": "M hosts/s",
-        "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(tuned_ms, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8->f64->f32",
-        "data": "synthetic (register-level)",
-        "config": {"workload": "batched 4M hosts c~logU(1,1e7) g in {64..512} Z=2^26 k=60",
-                   "hosts": H, "Z": Z, "k": k, "virtual_registers": gathers},
         "persistent_autotuned_ms": round(tuned_ms, 4), "autotuned_shape": [lanes, threads],
         "persistent_default_ms": round(default_ms, 4),
         "per_group_launches_ms": round(per_group_ms, 4),
@@ -527,17 +617,35 @@ def run_batched(a):
         "gathers_per_s": round(gathers / (tuned_ms * 1e-3) / 1e9, 2),
         "planned_ms": round(planned_ms, 4), "planned_equals_gather": planned_same,
         "plan": plan_info,
-        "accuracy": {"mre_vs_truth": float(rel.mean()), "median_rel_err": float(np.median(rel))},
-        "gpu_launches": a.steps,
+        "accuracy": {"mre_vs_truth": float(rel.mean()), "median_rel_err": float(np.median(rel)),
+                     "items_per_register": round(load, 1),
+                     "note": ("sum of cardinalities / Z = items per physical register: the "
+                              "pool is saturated, so the noise term dominates every host "
+                              "below about g times that load")},
+        "steps": a.steps, "warmup": a.warmup,
         "clocks": clk.summary(),
     }
+
+
+def run_batched(a):
+    r = batched_core(a)
+    line = {
+        "metric": "batched estimate: hosts/s (one persistent autotuned launch)",
+        "value": r["value"], "unit": r["unit"],
+        "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": r["persistent_autotuned_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8->f64->f32",
+        "data": "synthetic (register-level)",
+        "config": {"workload": r["workload"], "hosts": r["hosts"], "Z": r["Z"], "k": r["k"],
+                   "virtual_registers": r["virtual_registers"]},
+        "gpu_launches": a.steps, "clocks": r.pop("clocks"),
+    }
+    line.update({k: v for k, v in r.items() if k not in line and k != "workload"})
     print(json.dumps(line), flush=True)
-    v.close()
 
 
 # ------------------------------------------------------ streaming service arm
 
-def run_serve(a):
+def serve_core(a, tenants, slices_per_tenant, warmup):
     """Streaming service: slices of log-uniform size in [1M, 128M] pairs
     (8M active hosts, Zipf 1.1 host weights, bursty superspreaders at 0.01%),
     k = 30, Z = 2^26, g = 256; every slice is one CUDA graph replay of scan +
@@ -550,14 +658,14 @@ def run_serve(a):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     wl = traffic.STREAM
     rng = np.random.default_rng(7)
-    tenants = []
-    for t in range(a.tenants):
+    tdata = []
+    for t in range(tenants):
         st = traffic.StreamingTraffic(wl["n_hosts"], wl["zipf_s"], seed=500 + t)
         pool = torch.from_numpy(st.make_pool(wl["n_hi"]).view(np.int32)).pin_memory()
-        n_all = a.warmup + a.slices_per_tenant
+        n_all = warmup + slices_per_tenant
         sizes = traffic.log_uniform_sizes(rng, n_all, wl["n_lo"], wl["n_hi"])
         offs = [int(rng.integers(0, wl["n_hi"] - n + 1)) for n in sizes]
-        tenants.append((st.aips, pool, sizes, offs))
+        tdata.append((st.aips, pool, sizes, offs))
     mlp = None
     wpath = os.path.join(ROOT, "paper_1810_13132_gb300", "weights", "correction_trace.npz")
     if os.path.exists(wpath) and not a.no_learned:
@@ -565,132 +673,175 @@ def run_serve(a):
         mlp = Mlp(seed=1)
         mlp.set_params(wz["params"], float(wz["nmax"]))
     cfg = Config(k=wl["k"], num_bdr=wl["Z"], log2_g=wl["log2_g"], seed=SEED)
-    srv = Server(budget_bytes=240 << 30, max_tenants=max(4, a.tenants))
+    srv = Server(budget_bytes=240 << 30, max_tenants=max(4, tenants))
     lat = {"device": [], "e2e": []}
     pairs_done = [0]
     lock = threading.Lock()
-    start_evt = threading.Barrier(a.tenants + 1)
+    start_evt = threading.Barrier(tenants + 1)
+    errors = []
 
     def worker(i):
-        aips, pool, sizes, offs = tenants[i]
-        t = srv.open(cfg, wl["n_hi"], aips, mlp=mlp)
-        out = np.empty(aips.size, dtype=np.float32)
-        pending = []
+        try:
+            aips, pool, sizes, offs = tdata[i]
+            t = srv.open(cfg, wl["n_hi"], aips, mlp=mlp)
+            out = np.empty(aips.size, dtype=np.float32)
+            pending = []
 
-        def run(j, timed):
-            pending.append((srv.submit(t, pool[offs[j]:offs[j] + int(sizes[j])]), j, timed))
-            if len(pending) == 2:
+            def run(j, timed):
+                pending.append((srv.submit(t, pool[offs[j]:offs[j] + int(sizes[j])]), j, timed))
+                if len(pending) == 2:
+                    tk, jj, tt = pending.pop(0)
+                    dms, ems = srv.wait(t, tk, out)
+                    if tt:
+                        with lock:
+                            lat["device"].append(dms)
+                            lat["e2e"].append(ems)
+                            pairs_done[0] += int(sizes[jj])
+
+            for j in range(warmup):
+                run(j, False)
+            while pending:
+                srv.wait(t, pending.pop(0)[0], out)
+            start_evt.wait()
+            for j in range(warmup, warmup + slices_per_tenant):
+                run(j, True)
+            while pending:
                 tk, jj, tt = pending.pop(0)
                 dms, ems = srv.wait(t, tk, out)
-                if tt:
-                    with lock:
-                        lat["device"].append(dms)
-                        lat["e2e"].append(ems)
-                        pairs_done[0] += int(sizes[jj])
+                with lock:
+                    lat["device"].append(dms)
+                    lat["e2e"].append(ems)
+                    pairs_done[0] += int(sizes[jj])
+            srv.close_tenant(t)
+        except Exception as e:  # reported by the caller
+            errors.append(repr(e))
+            start_evt.abort()
 
-        for j in range(a.warmup):
-            run(j, False)
-        while pending:
-            srv.wait(t, pending.pop(0)[0], out)
-        start_evt.wait()
-        for j in range(a.warmup, a.warmup + a.slices_per_tenant):
-            run(j, True)
-        while pending:
-            tk, jj, tt = pending.pop(0)
-            dms, ems = srv.wait(t, tk, out)
-            with lock:
-                lat["device"].append(dms)
-                lat["e2e"].append(ems)
-                pairs_done[0] += int(sizes[jj])
-        srv.close_tenant(t)
-
-    th = [threading.Thread(target=worker, args=(i,)) for i in range(a.tenants)]
+    th = [threading.Thread(target=worker, args=(i,)) for i in range(tenants)]
     for x in th:
         x.start()
-    start_evt.wait()
+    try:
+        start_evt.wait()
+    except threading.BrokenBarrierError:
+        pass
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         t0 = time.perf_counter()
         for x in th:
             x.join()
         wall = time.perf_counter() - t0
+    srv.close()
+    if errors:
+        raise RuntimeError("; ".join(errors))
     dev = np.array(lat["device"])
     e2e = np.array(lat["e2e"])
-    line = {
-        "metric": "streaming service: sustained G pairs/s; p50/p99 slice latency",
+    return {
+        "workload": wl["name"], "tenants": tenants, "hosts_per_tenant": wl["n_hosts"],
+        "learned_correction": mlp is not None,
         "value": round(pairs_done[0] / wall / 1e9, 3), "unit": "G pairs/s",
-        "n_gpus": 1, "steps": len(dev), "warmup": a.warmup * a.tenants,
-        "ms_per_step": round(float(np.mean(e2e)), 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": wl["name"], "tenants": a.tenants, "hosts_per_tenant": wl["n_hosts"],
-                   "learned_correction": mlp is not None},
-        "latency_ms": {"device_p50": float(np.percentile(dev, 50)), "device_p99": float(np.percentile(dev, 99)),
-                       "e2e_p50": float(np.percentile(e2e, 50)), "e2e_p99": float(np.percentile(e2e, 99))},
+        "slices": int(len(dev)), "warmup_slices": warmup * tenants,
+        "latency_ms": {"device_p50": float(np.percentile(dev, 50)),
+                       "device_p99": float(np.percentile(dev, 99)),
+                       "e2e_p50": float(np.percentile(e2e, 50)),
+                       "e2e_p99": float(np.percentile(e2e, 99)),
+                       "e2e_mean": float(np.mean(e2e))},
         "pairs": pairs_done[0], "wall_s": round(wall, 3),
-        "gpu_launches": int(len(dev) * 4),
         "clocks": clk.summary(),
     }
+
+
+def run_serve(a):
+    r = serve_core(a, a.tenants, a.slices_per_tenant, a.warmup)
+    line = {
+        "metric": "streaming service: sustained G pairs/s; p50/p99 slice latency",
+        "value": r["value"], "unit": "G pairs/s",
+        "n_gpus": 1, "steps": r["slices"], "warmup": r["warmup_slices"],
+        "ms_per_step": round(r["latency_ms"]["e2e_mean"], 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": r["workload"], "tenants": r["tenants"],
+                   "hosts_per_tenant": r["hosts_per_tenant"],
+                   "learned_correction": r["learned_correction"]},
+        "latency_ms": r["latency_ms"], "pairs": r["pairs"], "wall_s": r["wall_s"],
+        "gpu_launches": int(r["slices"] * 4), "clocks": r["clocks"],
+    }
     print(json.dumps(line), flush=True)
-    srv.close()
 
 
 # ------------------------------------------------- oracle (CPU) timings
 
-def _oracle_step_times(wl, gen, slices, n_pairs_sample, n_hosts_sample):
-    """One step of the single-threaded oracle on a bounded sample: scan
-    n_pairs_sample pairs, a full slide of all Z BDRs, estimates of
-    n_hosts_sample hosts; returns seconds per pair, per slide, per host."""
+def _oracle_full_step(wl, hosts, pairs):
+    """One complete step of the single-threaded oracle: scan the slice's
+    pairs, slide, estimate every host.  Returns (scan, slide, estimate)
+    seconds, each measured."""
     import oracle
     o = oracle.Oracle("gfast", k=wl["k"], Z=wl["Z"], b=wl["log2_g"], seed=SEED)
-    s = slices[0][:n_pairs_sample]
-    t = time.perf_counter()
-    o.scan(s)
-    t_scan = time.perf_counter() - t
-    t = time.perf_counter()
+    t0 = time.perf_counter()
+    o.scan(pairs)
+    t1 = time.perf_counter()
     o.slide()
-    t_slide = time.perf_counter() - t
-    hs = gen.aips[:n_hosts_sample]
-    t = time.perf_counter()
-    o.estimate(hs)
-    t_est = time.perf_counter() - t
-    return t_scan / len(s), t_slide, t_est / len(hs)
+    t2 = time.perf_counter()
+    o.estimate(hosts)
+    t3 = time.perf_counter()
+    return t1 - t0, t2 - t1, t3 - t2
 
 
 def cpu_baseline(wl, gen, slices):
+    """The oracle (plain single-threaded C, one host core) on one full step of
+    the same workload -- the first trace slice, one slide of all Z BDRs,
+    estimates of all H hosts -- timed whole.  A sampled step (4M pairs, full
+    slide, 50k hosts, scaled up) is reported beside it as a cross-check."""
+    ts, tl, te = _oracle_full_step(wl, gen.aips, slices[0])
+    step_s = ts + tl + te
     ns, nh = min(4_000_000, wl["n_pairs"]), min(50_000, wl["n_hosts"])
-    per_pair, slide_s, per_host = _oracle_step_times(wl, gen, slices, ns, nh)
-    step_s = per_pair * wl["n_pairs"] + slide_s + per_host * wl["n_hosts"]
+    ss, sl, se = _oracle_full_step(wl, gen.aips[:nh], slices[1 % len(slices)][:ns])
+    sampled = ss * wl["n_pairs"] / ns + sl + se * wl["n_hosts"] / nh
     return {"value": round(wl["n_pairs"] / step_s / 1e9, 6), "unit": "G pairs/s", "cores": 1,
             "kind": "oracle",
-            "sample": f"single-threaded C oracle (gfast): scan of {ns} pairs, one full slide of "
-                      f"Z={wl['Z']} BDRs, estimates of {nh} hosts; step time scaled to "
-                      f"{wl['n_pairs']} pairs and {wl['n_hosts']} hosts",
-            "step_s": round(step_s, 3)}
+            "sample": (f"one full step, measured: single-threaded C oracle (gfast) scanning all "
+                       f"{wl['n_pairs']} pairs of a trace slice, one slide of Z={wl['Z']} BDRs, "
+                       f"estimates of all {wl['n_hosts']} hosts"),
+            "step_s": round(step_s, 3),
+            "parts_s": {"scan": round(ts, 3), "slide": round(tl, 3), "estimate": round(te, 3)},
+            "cross_check": {"sampled_step_s": round(sampled, 3),
+                            "sample": f"scan {ns} pairs, full slide, {nh} hosts, scaled"}}
+
+
+REF_SCALE = 4  # the reference arm's step: the trace workload at 1/4 scale
 
 
 def run_reference(a):
+    """The oracle as the reference arm: each step is one complete oracle step
+    (scan, slide, estimate of every host) of the trace workload at 1/4 scale
+    -- 16M pairs per slice, 250k hosts, Z = 2^22, the same cardinality law
+    scaled so that the load per register and per pair is the trace's -- on
+    one host core, timed whole; ms_per_step is that measured time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     wl = _workload(a.workload)
-    gen, slices = _make_inputs(wl, seed=1000, n_slices=1)
-    ns, nh = min(2_000_000, wl["n_pairs"]), min(20_000, wl["n_hosts"])
+    if a.workload == "trace":
+        wl.update(n_pairs=wl["n_pairs"] // REF_SCALE, n_hosts=wl["n_hosts"] // REF_SCALE,
+                  c_max=wl["c_max"] // REF_SCALE, Z=wl["Z"] // REF_SCALE)
+    gen, slices = _make_inputs(wl, seed=1000, n_slices=2)
     steps = []
     t_all = time.perf_counter()
     for i in range(a.warmup + a.steps):
-        per_pair, slide_s, per_host = _oracle_step_times(wl, gen, slices, ns, nh)
+        ts, tl, te = _oracle_full_step(wl, gen.aips, slices[i % 2])
         if i >= a.warmup:
-            steps.append(per_pair * wl["n_pairs"] + slide_s + per_host * wl["n_hosts"])
+            steps.append(ts + tl + te)
     step_s = statistics.mean(steps)
     value = wl["n_pairs"] / step_s / 1e9
+    sample = (f"per step: one complete oracle step of the trace workload at 1/{REF_SCALE} scale "
+              f"({wl['n_pairs']} pairs, Z={wl['Z']}, {wl['n_hosts']} hosts), timed whole"
+              if a.workload == "trace" else "per step: one complete oracle step")
     line = {
         "impl": "reference", "metric": _metric_name(), "value": round(value, 6),
         "unit": "G pairs/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": round(step_s * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": wl["name"] + " gfast"},
+        "config": {"workload": _workload(a.workload)["name"] + " gfast",
+                   "reference_step": sample},
         "cpu_baseline": {"value": round(value, 6), "unit": "G pairs/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: scan of {ns} pairs, full slide of Z={wl['Z']}, "
-                                   f"estimates of {nh} hosts, scaled to the full step"},
+                         "sample": sample},
         "e2e": {"value": round(value, 6), "unit": "G pairs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "wall_s": round(time.perf_counter() - t_all, 1),

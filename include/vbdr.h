@@ -260,6 +260,67 @@ VBDR_API int vbdr_estimate_registers_noalloc(const uint8_t *d_reg, uint64_t num_
                                              const uint32_t *d_aips, uint64_t n_hosts,
                                              float *d_out, void *stream);
 
+/* ---- several GPUs --------------------------------------------------------
+ * The paper's scan is data parallel over pairs and its slide over BDRs
+ * (Sec. 4.2): every update ORs a bsLBP1 bit (Alg. 7), zeroes a DR (Alg. 9)
+ * or raises nowLBP1 (Alg. 4), all commutative and idempotent.  A pool spread
+ * over ranks therefore needs only these exchanges, which the caller performs
+ * with any transport (NCCL, ...); the calls below read and write device
+ * buffers of one handle on its own device.
+ *   Pair-sharded replicas: every rank scans its share of a slice into a full
+ *   replica, the ranks exchange their slice states and merge them with
+ *   vbdr_merge_slice_state before the slide, and every rank slides the same
+ *   merged state.
+ *   Pool-partitioned: rank r owns BDRs [r Zr, (r+1) Zr), Zr = ceil(Z / ranks);
+ *   every rank turns its pairs into records with vbdr_route_records, the
+ *   ranks exchange the groups (all-to-all), each applies what it received
+ *   with vbdr_apply_records and slides; the byte-wise maximum of the ranks'
+ *   register arrays (every register outside a rank's range is 0 there) is
+ *   the pool's, installed on every rank with vbdr_set_registers. */
+
+/* Device pointers of the handle's state, owned by the handle (valid until
+ * vbdr_destroy; read them only between calls that write them):
+ * d_slice_state / slice_words: the state a scan updates, as 32-bit words --
+ * bsLBP1 [Z] (gfast), the DRV planes [P][Zs] (gsmall), nowLBP1 bytes [Zs] as
+ * Zs/4 words (serial); d_reg: the Z registers of the last slide; d_pcsa: the
+ * Z PCSA statistics (gsmall, else NULL).  Any output may be NULL.
+ * Errors: VBDR_EINVAL (NULL handle). */
+VBDR_API int vbdr_state_pointers(vbdr_t h, uint32_t **d_slice_state, uint64_t *slice_words,
+                                 uint8_t **d_reg, uint8_t **d_pcsa);
+
+/* Hash n pairs (d_pairs as in vbdr_scan_slice, 4-byte aligned suffices) into
+ * records pidx << 5 | (LBP1 - 1) (Alg. 4 and Alg. 3), grouped by the rank
+ * owning pidx: group r is d_recs[r cap, r cap + min(d_fill[r], cap)), in no
+ * particular order.  d_recs: device, n_ranks * cap uint32; d_fill: device,
+ * n_ranks uint64 (8-byte aligned), set by the call; d_fill[r] > cap means
+ * group r overflowed and records were dropped -- size cap for the worst
+ * case (cap = n always suffices).  Requires Z <= 2^27 and every g <= 512.
+ * The state is not changed.  Errors: VBDR_EINVAL (NULL or misaligned
+ * pointer, n_ranks not in 1..256, Z > 2^27), VBDR_ERANGE (g above 512),
+ * VBDR_ECUDA. */
+VBDR_API int vbdr_route_records(vbdr_t h, const uint32_t *d_pairs, uint64_t n, uint32_t n_ranks,
+                                uint32_t *d_recs, uint64_t cap, uint64_t *d_fill, void *stream);
+
+/* Apply n records pidx << 5 | (LBP1 - 1) (from vbdr_route_records, on any
+ * rank) to the handle's slice state: the same update the scan of their pairs
+ * makes (Alg. 7, Alg. 9 or Alg. 4).  d_recs: device, 4-byte aligned.
+ * Errors: VBDR_EINVAL (NULL or misaligned, Z > 2^27), VBDR_ECUDA. */
+VBDR_API int vbdr_apply_records(vbdr_t h, const uint32_t *d_recs, uint64_t n, void *stream);
+
+/* Merge another replica's slice state (same configuration; d_other: device,
+ * slice_words words laid out as vbdr_state_pointers gives them) into this
+ * handle's: OR of bsLBP1 (gfast), field-wise minimum of the DRs (gsmall),
+ * maximum of nowLBP1 (serial).  Errors: VBDR_EINVAL, VBDR_ECUDA. */
+VBDR_API int vbdr_merge_slice_state(vbdr_t h, const uint32_t *d_other, void *stream);
+
+/* Install Z registers (d_reg, device) and, for gsmall, the Z PCSA statistics
+ * (d_pcsa, device, may be NULL) as the registers of the last slide, and
+ * recompute the pool sums the estimators read (Sec. 4.1's noise term).
+ * The next slide overwrites them.  Errors: VBDR_EINVAL (NULL d_reg, d_pcsa
+ * on a layout without PCSA statistics), VBDR_ECUDA. */
+VBDR_API int vbdr_set_registers(vbdr_t h, const uint8_t *d_reg, const uint8_t *d_pcsa,
+                                void *stream);
+
 /* Register-level state for workloads too large to scan (batched estimation
  * over millions of hosts): the register array becomes, for every physical
  * BDR, the largest value among the virtual registers that Alg. 3 maps onto
@@ -415,6 +476,14 @@ VBDR_API int vbdr_server_wait(vbdr_server_t s, uint32_t tenant, uint64_t ticket,
 
 /* Device bytes and tenants currently admitted. */
 VBDR_API int vbdr_server_in_use(vbdr_server_t s, uint64_t *bytes, uint32_t *tenants);
+
+/* The handle that holds a tenant's BDR state (owned by the server: never
+ * destroy it), for inspection with vbdr_copy_state / vbdr_copy_pool_sums /
+ * vbdr_save once every submitted slice of the tenant has been waited for
+ * (the state then reflects all of them; between submit and wait it is in
+ * flight on the tenant's streams).  Valid until vbdr_server_close of the
+ * tenant.  Errors: VBDR_EINVAL (no such tenant, NULL out). */
+VBDR_API int vbdr_server_tenant_handle(vbdr_server_t s, uint32_t tenant, vbdr_t *out);
 
 /* ---- checkpoint / resume ----
  * The complete state of a handle -- configuration, DRV, the slice state

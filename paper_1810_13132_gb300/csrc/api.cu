@@ -48,6 +48,7 @@ struct vbdr {
   uint64_t est_cap;
   uint16_t *d_feat;     // feature rows of the learned estimate [feat_cap][48]
   uint64_t feat_cap;
+  vbk::BucketDev bk;    // record buckets of the bucketed scan (bk.recs null: not used)
 };
 
 // A host list's estimate plan (plan.cu): device arrays plus the handle
@@ -166,6 +167,34 @@ void free_state(vbdr *h) {
   cudaFree(h->d_aips);
   cudaFree(h->d_out);
   cudaFree(h->d_feat);
+  cudaFree(h->bk.recs);
+  cudaFree(h->bk.fill);
+}
+
+// Slices of at least this many pairs take the bucketed scan (bucket.cu); its
+// apply pass costs a fixed amount per non-empty pool tile, which smaller
+// slices do not repay.
+constexpr uint64_t kBucketMinPairs = 1ull << 18;
+
+// Record capacity of the bucketed scan: at most 2^24 records (64 MiB, so
+// that one pass's records stay in L2), at least 2^20, else one 2^16-record
+// bucket per tile; a pass routes two thirds of the capacity, which leaves
+// every bucket 50% headroom over its mean load.
+void bucket_sizes(const Dims &d, uint32_t *ntiles, uint32_t *cap, uint64_t *pass_pairs) {
+  const uint64_t nt = (d.Z + vbk::kBucketTile - 1) / vbk::kBucketTile;
+  uint64_t total = nt * vbk::kBucketTile;
+  total = std::min<uint64_t>(std::max<uint64_t>(total, 1ull << 20), 1ull << 24);
+  *ntiles = (uint32_t)nt;
+  *cap = (uint32_t)(total / nt);
+  *pass_pairs = (total * 2 / 3) & ~((1ull << 14) - 1);
+}
+
+// The scan of n pairs (n_dev: device-side count up to n, for graphs).
+cudaError_t scan_any(vbdr *h, const uint32_t *pairs, uint64_t n, cudaStream_t st,
+                     const uint64_t *n_dev = nullptr) {
+  if (h->bk.recs && n >= kBucketMinPairs)
+    return vbk::launch_scan_bucketed(h->d, h->s, h->bk, h->layout, pairs, n, st, n_dev);
+  return vbk::launch_scan(h->d, h->s, h->layout, pairs, n, st, n_dev);
 }
 
 }  // namespace
@@ -250,6 +279,12 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->s.lnv, vbk::kLnTab * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.sums, vbk::kSums * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.check, sizeof(unsigned int));
+  if (e == cudaSuccess && vbk::bucket_scan_applies(d, h->layout)) {
+    bucket_sizes(d, &h->bk.ntiles, &h->bk.cap, &h->bk.pass_pairs);
+    e = cudaMalloc(&h->bk.recs, (size_t)h->bk.ntiles * h->bk.cap * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&h->bk.fill, (size_t)h->bk.ntiles * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(h->bk.fill, 0, (size_t)h->bk.ntiles * sizeof(uint32_t));
+  }
   if (e == cudaSuccess) {
     double lnv[vbk::kLnTab];
     lnv[0] = 0.0;
@@ -298,8 +333,7 @@ int vbdr_scan_slice(vbdr_t h, const uint32_t *d_pairs, uint64_t n, void *stream)
   if (h->sticky) return h->sticky;
   if (n == 0) return VBDR_OK;
   if (!d_pairs || ((uintptr_t)d_pairs & 15u)) return VBDR_EINVAL;
-  return fail_cuda(h, vbk::launch_scan(h->d, h->s, h->layout,
-                                        d_pairs, n, (cudaStream_t)stream));
+  return fail_cuda(h, scan_any(h, d_pairs, n, (cudaStream_t)stream));
 }
 
 int vbdr_scan_slice_devn(vbdr_t h, const uint32_t *d_pairs, const uint64_t *d_n,
@@ -309,8 +343,7 @@ int vbdr_scan_slice_devn(vbdr_t h, const uint32_t *d_pairs, const uint64_t *d_n,
   if (h->sticky) return h->sticky;
   if (max_n == 0) return VBDR_OK;
   if (!d_pairs || !d_n || ((uintptr_t)d_pairs & 15u) || ((uintptr_t)d_n & 7u)) return VBDR_EINVAL;
-  return fail_cuda(h, vbk::launch_scan(h->d, h->s, h->layout, d_pairs, max_n,
-                                       (cudaStream_t)stream, d_n));
+  return fail_cuda(h, scan_any(h, d_pairs, max_n, (cudaStream_t)stream, d_n));
 }
 
 int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n, void *stream) {
@@ -355,7 +388,7 @@ int vbdr_scan_slice_host(vbdr_t h, const uint32_t *h_pairs, uint64_t n, void *st
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[buf], h->copy_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_copied[buf], 0);
     if (e != cudaSuccess) return fail_cuda(h, e);
-    e = vbk::launch_scan(h->d, h->s, h->layout, h->stage[buf], cnt, st);
+    e = scan_any(h, h->stage[buf], cnt, st);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_free[buf], st);
     if (e != cudaSuccess) return fail_cuda(h, e);
     done += cnt;
@@ -745,6 +778,91 @@ int vbdr_copy_pcsa(vbdr_t h, uint8_t *h_pcsa, void *stream) {
                                   (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   return fail_cuda(h, e);
+}
+
+/* ------------------------------------------------------- several GPUs */
+
+namespace {
+// The slice state the replicas merge: bsLBP1 (gfast), the DRV (gsmall; the
+// scan zeroes DRs in place), nowLBP1 as words (serial).
+void slice_state_of(const vbdr *h, uint32_t **ptr, uint64_t *words) {
+  if (h->layout == VBDR_GFAST) {
+    *ptr = h->s.bs;
+    *words = h->d.Z;
+  } else if (h->layout == VBDR_GSMALL) {
+    *ptr = h->s.drv;
+    *words = (uint64_t)h->d.P * h->d.Zs;
+  } else {
+    *ptr = reinterpret_cast<uint32_t *>(h->s.now);
+    *words = h->d.Zs / 4;
+  }
+}
+}  // namespace
+
+int vbdr_state_pointers(vbdr_t h, uint32_t **d_slice_state, uint64_t *slice_words,
+                        uint8_t **d_reg, uint8_t **d_pcsa) {
+  if (!h) return VBDR_EINVAL;
+  uint32_t *p = nullptr;
+  uint64_t w = 0;
+  slice_state_of(h, &p, &w);
+  if (d_slice_state) *d_slice_state = p;
+  if (slice_words) *slice_words = w;
+  if (d_reg) *d_reg = h->s.reg;
+  if (d_pcsa) *d_pcsa = h->s.pcsa;
+  return VBDR_OK;
+}
+
+int vbdr_route_records(vbdr_t h, const uint32_t *d_pairs, uint64_t n, uint32_t n_ranks,
+                       uint32_t *d_recs, uint64_t cap, uint64_t *d_fill, void *stream) {
+  NvtxRange nvtx("vbdr_route_records");
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (n_ranks < 1 || n_ranks > vbk::kMaxRanks || h->d.Z > (1ull << 27)) return VBDR_EINVAL;
+  if (!d_fill || ((uintptr_t)d_fill & 7u)) return VBDR_EINVAL;
+  if (n && (!d_pairs || !d_recs || ((uintptr_t)d_pairs & 3u) || ((uintptr_t)d_recs & 3u)))
+    return VBDR_EINVAL;
+  if ((h->d.group_rule ? 1u << (h->d.b_min + 3) : 1u << h->d.b) > (uint32_t)vbk::kKtabSize)
+    return VBDR_ERANGE;
+  return fail_cuda(h, vbk::launch_route_records(h->d, h->s, d_pairs, n, n_ranks, d_recs, cap,
+                                                reinterpret_cast<unsigned long long *>(d_fill),
+                                                (cudaStream_t)stream));
+}
+
+int vbdr_apply_records(vbdr_t h, const uint32_t *d_recs, uint64_t n, void *stream) {
+  NvtxRange nvtx("vbdr_apply_records");
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (n == 0) return VBDR_OK;
+  if (!d_recs || ((uintptr_t)d_recs & 3u) || h->d.Z > (1ull << 27)) return VBDR_EINVAL;
+  return fail_cuda(h, vbk::launch_apply_records(h->d, h->s, h->layout, d_recs, n,
+                                                (cudaStream_t)stream));
+}
+
+int vbdr_merge_slice_state(vbdr_t h, const uint32_t *d_other, void *stream) {
+  NvtxRange nvtx("vbdr_merge_slice_state");
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!d_other || ((uintptr_t)d_other & 3u)) return VBDR_EINVAL;
+  uint32_t *p = nullptr;
+  uint64_t w = 0;
+  slice_state_of(h, &p, &w);
+  return fail_cuda(h, vbk::launch_merge_slice_state(h->d, h->s, h->layout, d_other, w,
+                                                    (cudaStream_t)stream));
+}
+
+int vbdr_set_registers(vbdr_t h, const uint8_t *d_reg, const uint8_t *d_pcsa, void *stream) {
+  NvtxRange nvtx("vbdr_set_registers");
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!d_reg || (d_pcsa && !h->s.pcsa)) return VBDR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(h->s.reg, d_reg, h->d.Z, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && d_pcsa)
+    e = cudaMemcpyAsync(h->s.pcsa, d_pcsa, h->d.Z, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = vbk::launch_pool_sums(h->s.reg, h->s.pcsa, h->d.Z, h->s.sums, st);
+  int rc = fail_cuda(h, e);
+  if (rc == VBDR_OK) h->slid = true;
+  return rc;
 }
 
 /* ---------------------------------------------------------------- plans */

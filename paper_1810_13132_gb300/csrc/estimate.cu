@@ -114,9 +114,10 @@ __global__ void __launch_bounds__(kMaxEstWarps * 32)
             if (vbk_check(pidx < d.Z, s.check, kChkPidx)) {
               M[u] = __ldg(vals + pidx);
               // the checked build skips and records a value above 32; the
-              // plain build reads it as 32 (registers a caller supplies)
+              // plain estimate of the normal build reads it as 32 (registers
+              // a caller supplies; the handle's own never exceed 32)
               if (!vbk_check(M[u] <= 32u, s.check, kChkReg)) M[u] = 0xffu;
-              else M[u] = min(M[u], 32u);
+              else if constexpr (MODE == kPlain) M[u] = min(M[u], 32u);
             }
           }
         }

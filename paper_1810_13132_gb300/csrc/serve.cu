@@ -139,6 +139,10 @@ uint64_t vbdr_server_tenant_bytes(const vbdr_config *cfg, uint64_t max_pairs, ui
                    (cfg->layout == VBDR_SERIAL ? Zs : 0) +
                    (cfg->layout == VBDR_GSMALL ? Zs : 0);  // PCSA statistics
   bytes += 64ull << 10;                                // tables, sums
+  if (cfg->layout != VBDR_SERIAL) {                    // record buckets of the bucketed scan
+    const uint64_t nt = (cfg->num_bdr + 65535) / 65536;
+    bytes += 4 * std::min<uint64_t>(std::max<uint64_t>(nt * 65536, 1ull << 20), 1ull << 24) + 4 * nt;
+  }
   bytes += 2 * (max_pairs * 8 + 8 + n_hosts * 4);      // staging slots
   bytes += n_hosts * 4;                                // host list
   return bytes;
@@ -318,6 +322,14 @@ int vbdr_server_in_use(vbdr_server_t s, uint64_t *bytes, uint32_t *tenants) {
     for (const Tenant &t : s->tenants) c += t.used;
     *tenants = c;
   }
+  return VBDR_OK;
+}
+
+int vbdr_server_tenant_handle(vbdr_server_t s, uint32_t tenant, vbdr_t *out) {
+  if (!out) return VBDR_EINVAL;
+  *out = nullptr;
+  if (!s || tenant >= s->tenants.size() || !s->tenants[tenant].used) return VBDR_EINVAL;
+  *out = s->tenants[tenant].h;
   return VBDR_OK;
 }
 

@@ -232,6 +232,36 @@ cudaError_t launch_estimate_alt(const Dims &d, const DevState &s, const EstConst
                                 const uint32_t *aips, uint64_t n, float *out, int which,
                                 cudaStream_t st, EstLaunch cfg);
 
+// ----- bucketed scan (bucket.cu) -----
+// Pool tiles of 2^16 BDRs; a slice's pairs become 4-byte records
+// (pidx mod 2^16) << 5 | (LBP1 - 1) in their tile's bucket, then each tile
+// applies its bucket in shared memory.  Records of one tile occupy
+// recs[t cap, t cap + min(fill[t], cap)).
+constexpr uint32_t kBucketTileLog2 = 16;
+constexpr uint32_t kBucketTile = 1u << kBucketTileLog2;
+constexpr uint32_t kMaxBucketTiles = 2048;  // Z <= 2^27
+struct BucketDev {
+  uint32_t *recs;       // [ntiles][cap]
+  uint32_t *fill;       // [ntiles], zero between passes
+  uint32_t ntiles;
+  uint32_t cap;         // records per bucket
+  uint64_t pass_pairs;  // pairs routed per pass (a multiple of the route batch)
+};
+bool bucket_scan_applies(const Dims &d, int layout);
+cudaError_t launch_scan_bucketed(const Dims &d, const DevState &s, const BucketDev &bk, int layout,
+                                 const uint32_t *pairs, uint64_t n, cudaStream_t st,
+                                 const uint64_t *n_dev = nullptr);
+
+// ----- several GPUs (shard.cu) -----
+constexpr uint32_t kMaxRanks = 256;
+cudaError_t launch_route_records(const Dims &d, const DevState &s, const uint32_t *pairs, uint64_t n,
+                                 uint32_t ranks, uint32_t *recs, uint64_t cap,
+                                 unsigned long long *fill, cudaStream_t st);
+cudaError_t launch_apply_records(const Dims &d, const DevState &s, int layout, const uint32_t *recs,
+                                 uint64_t n, cudaStream_t st);
+cudaError_t launch_merge_slice_state(const Dims &d, const DevState &s, int layout,
+                                     const uint32_t *other, uint64_t words, cudaStream_t st);
+
 // ----- estimate plans (plan.cu) -----
 // Register chunk of the planned estimate: 2^15 BDRs (32 KiB of reg); the
 // register array is allocated in whole chunks.

@@ -92,9 +92,16 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "vbdr_server_in_use": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U32)]),
+    "vbdr_server_tenant_handle": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(_VP)]),
     "vbdr_state_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(_U64)]),
     "vbdr_save": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
     "vbdr_load": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
+    "vbdr_state_pointers": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_U64),
+                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "vbdr_route_records": (ctypes.c_int, [_VP, _VP, _U64, _U32, _VP, _U64, _VP, _VP]),
+    "vbdr_apply_records": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
+    "vbdr_merge_slice_state": (ctypes.c_int, [_VP, _VP, _VP]),
+    "vbdr_set_registers": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "vbdr_estimate_registers_noalloc": (ctypes.c_int, [_VP, _U64, _U32, _U64, _VP, _U64, _VP,
                                                        _VP]),
 }
@@ -176,16 +183,20 @@ class Vbdr:
     estimates on the device.  Calls run on the current torch CUDA stream.
     """
 
-    def __init__(self, cfg: Config):
+    def __init__(self, cfg: Config, _borrowed=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("VBDR needs a CUDA GPU; no CPU fallback exists")
         torch.cuda.init()
         self.cfg = cfg
         self._L = load()
-        h = ctypes.c_void_p()
-        c = cfg.to_c()
-        _check("vbdr_create", self._L.vbdr_create(ctypes.byref(c), ctypes.byref(h)))
+        self._owned = _borrowed is None
+        if _borrowed is None:
+            h = ctypes.c_void_p()
+            c = cfg.to_c()
+            _check("vbdr_create", self._L.vbdr_create(ctypes.byref(c), ctypes.byref(h)))
+        else:
+            h = _borrowed
         self._h = h
         R, w, P = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
         _check("vbdr_get_dims", self._L.vbdr_get_dims(h, ctypes.byref(R), ctypes.byref(w),
@@ -194,7 +205,8 @@ class Vbdr:
 
     def close(self) -> None:
         if getattr(self, "_h", None):
-            self._L.vbdr_destroy(self._h)
+            if self._owned:
+                self._L.vbdr_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -313,6 +325,71 @@ class Vbdr:
         _check("vbdr_estimate_learned", self._L.vbdr_estimate_learned(
             self._h, mlp._h, aips.data_ptr(), n, out.data_ptr(), _stream_ptr(stream)))
         return out
+
+    # -- several GPUs ---------------------------------------------------------------
+    def _pointers(self):
+        st, w, reg, pc = _VP(), _U64(), _VP(), _VP()
+        _check("vbdr_state_pointers", self._L.vbdr_state_pointers(
+            self._h, ctypes.byref(st), ctypes.byref(w), ctypes.byref(reg), ctypes.byref(pc)))
+        return st.value, w.value, reg.value, pc.value
+
+    def slice_state(self, stream=None):
+        """A copy (int32 CUDA tensor) of the slice state the replicas merge."""
+        ptr, words, _, _ = self._pointers()
+        return _device_copy(ptr, words, "<i4")
+
+    def merge_slice_state(self, other, stream=None) -> None:
+        """Merge another replica's slice state (int32 CUDA tensor laid out as
+        slice_state() returns it) into this handle's."""
+        ptr, words, _, _ = self._pointers()
+        assert other.is_cuda and other.is_contiguous() and other.numel() == words
+        assert other.dtype in (torch_int32(), torch_uint32())
+        _check("vbdr_merge_slice_state", self._L.vbdr_merge_slice_state(
+            self._h, other.data_ptr(), _stream_ptr(stream)))
+
+    def route_records(self, pairs, n_ranks: int, cap: int | None = None, stream=None):
+        """(records [n_ranks, cap] int32 CUDA tensor, fill [n_ranks] int64):
+        the pairs hashed into records pidx << 5 | (LBP1 - 1), grouped by the
+        rank owning pidx."""
+        import torch
+        assert pairs.is_cuda and pairs.is_contiguous()
+        n = pairs.numel() // 2
+        cap = n if cap is None else cap
+        recs = torch.empty((n_ranks, max(cap, 1)), dtype=torch.int32, device="cuda")
+        fill = torch.empty(n_ranks, dtype=torch.int64, device="cuda")
+        _check("vbdr_route_records", self._L.vbdr_route_records(
+            self._h, pairs.data_ptr() if n else None, n, n_ranks, recs.data_ptr(), cap,
+            fill.data_ptr(), _stream_ptr(stream)))
+        return recs, fill
+
+    def apply_records(self, recs, stream=None) -> None:
+        assert recs.is_cuda and recs.is_contiguous() and recs.dtype == torch_int32()
+        n = recs.numel()
+        _check("vbdr_apply_records", self._L.vbdr_apply_records(
+            self._h, recs.data_ptr() if n else None, n, _stream_ptr(stream)))
+
+    def registers_device(self):
+        """A copy (uint8 CUDA tensor) of the registers of the last slide."""
+        _, _, reg, _ = self._pointers()
+        return _device_copy(reg, self.cfg.num_bdr, "|u1")
+
+    def pcsa_device(self):
+        """A copy (uint8 CUDA tensor) of the PCSA statistics (gsmall)."""
+        _, _, _, pc = self._pointers()
+        assert pc, "PCSA statistics exist in the gsmall layout only"
+        return _device_copy(pc, self.cfg.num_bdr, "|u1")
+
+    def set_registers(self, reg, pcsa=None, stream=None) -> None:
+        """Install registers (uint8 CUDA tensor of Z values) and, for gsmall,
+        PCSA statistics; recomputes the pool sums."""
+        import torch
+        assert reg.is_cuda and reg.is_contiguous() and reg.dtype == torch.uint8
+        assert reg.numel() == self.cfg.num_bdr
+        if pcsa is not None:
+            assert pcsa.is_cuda and pcsa.is_contiguous() and pcsa.numel() == self.cfg.num_bdr
+        _check("vbdr_set_registers", self._L.vbdr_set_registers(
+            self._h, reg.data_ptr(), pcsa.data_ptr() if pcsa is not None else None,
+            _stream_ptr(stream)))
 
     # -- checkpoint / resume -------------------------------------------------------
     def save(self, stream=None) -> bytes:
@@ -463,6 +540,15 @@ class Server:
             ctypes.byref(dms), ctypes.byref(ems)))
         return dms.value, ems.value
 
+    def tenant_view(self, tenant: int, cfg: Config) -> "Vbdr":
+        """The tenant's state handle, borrowed from the server (inspection only,
+        once every submitted slice has been waited for; valid until the
+        tenant is closed)."""
+        h = ctypes.c_void_p()
+        _check("vbdr_server_tenant_handle", self._L.vbdr_server_tenant_handle(
+            self._h, tenant, ctypes.byref(h)))
+        return Vbdr(cfg, _borrowed=h)
+
     def in_use(self) -> tuple[int, int]:
         b, t = ctypes.c_uint64(), ctypes.c_uint32()
         _check("vbdr_server_in_use", self._L.vbdr_server_in_use(self._h, ctypes.byref(b),
@@ -558,6 +644,31 @@ def estimate_registers_noalloc(reg, num_bdr: int, log2_g: int, seed: int, aips, 
     _check("vbdr_estimate_registers_noalloc", L.vbdr_estimate_registers_noalloc(
         reg.data_ptr(), num_bdr, log2_g, seed, aips.data_ptr() if n else None, n,
         out.data_ptr() if n else None, _stream_ptr(stream)))
+
+
+def torch_int32():
+    import torch
+    return torch.int32
+
+
+def torch_uint32():
+    import torch
+    return torch.uint32
+
+
+class _DeviceView:
+    """A library-owned device buffer seen through the CUDA array interface."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def _device_copy(ptr: int, n: int, typestr: str):
+    """A torch copy of n elements of a library-owned device buffer."""
+    import torch
+    torch.cuda.synchronize()
+    return torch.as_tensor(_DeviceView(ptr, n, typestr), device="cuda").clone()
 
 
 def _host_ptr(a, width: int):

@@ -226,6 +226,35 @@ def test_all_layouts_agree_on_gpu():
     assert torch.equal(a.estimate(aips), c.estimate(aips))
 
 
+# ------------------------------------------------------ bucketed scan path
+# Slices of at least 2^18 pairs (gfast, gsmall) take the bucketed scan: pairs
+# become records in per-tile buckets that each pool tile applies in shared
+# memory.  These cases stress what is specific to it.
+
+@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+def test_bucketed_scan_bucket_overflow(layout):
+    """One host with g = 16: all records fall into at most 16 of the 16 pool
+    tiles, far above a bucket's share, so the overflowing records take the
+    direct path; several passes per slice (2M pairs)."""
+    rng = np.random.default_rng(120)
+    aip = np.array([0x01020304], dtype=np.uint32)
+    slices = [traffic.uniform_pairs(rng, 2_000_001, aip) for _ in range(3)]
+    _run(layout, 3, 1 << 20, 4, slices, aip)
+
+
+@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+def test_bucketed_scan_threshold_split_and_mixed_g(layout):
+    """Slices just below and at the bucketed-scan threshold, a slice scanned
+    in two calls that both take the bucketed path, mixed g, a pool that is
+    not a whole number of tiles; state after every scan and slide."""
+    rng = np.random.default_rng(121)
+    aips = traffic.distinct_u32(rng, 6000)
+    sizes = [(1 << 18) - 2, 1 << 18, 600_001, (1 << 18) + 1]
+    slices = [traffic.uniform_pairs(rng, n, aips) for n in sizes]
+    _run(layout, 7, (3 << 16) + 77, 6, slices[:2], aips, b_min=6, group_rule=1)
+    _run(layout, 7, (3 << 16) + 77, 6, slices[2:], aips, b_min=6, group_rule=1, split=2)
+
+
 # --------------------------------------------------------- host-buffer path
 
 @pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])

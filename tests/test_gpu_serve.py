@@ -2,7 +2,9 @@
 graph replay per slice, tenants overlapping on the device.  Each tenant's
 results must be the same alone and in the mix (the state update is
 order-independent and the estimate deterministic, so: bit for bit), equal to
-the direct handle API, and admission must wait for memory to free up."""
+the direct handle API and to the CPU oracle (estimates within 1e-6 of its
+FP64 values after every slice, registers and pool sums bit for bit), and
+admission must wait for memory to free up."""
 import threading
 import time
 
@@ -11,6 +13,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle  # noqa: E402
 from synth import traffic  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +42,8 @@ def _cfg(layout="gfast"):
     return Config(k=5, num_bdr=(1 << 16) + 3, log2_g=7, layout=layout, seed=SEED)
 
 
-def _run_tenant(srv, cfg, aips, slices, mlp=None, results=None, key=None, events=None):
+def _run_tenant(srv, cfg, aips, slices, mlp=None, results=None, key=None, events=None,
+                states=None):
     t = srv.open(cfg, 300_000, aips, mlp=mlp)
     if events is not None:
         events.append(("open", key, time.monotonic()))
@@ -56,6 +60,10 @@ def _run_tenant(srv, cfg, aips, slices, mlp=None, results=None, key=None, events
         outs.append(o)
     if events is not None:
         events.append(("close", key, time.monotonic()))
+    if states is not None:  # every slice has been waited for: the final state
+        view = srv.tenant_view(t, cfg)
+        states[key] = (view.registers(), view.pool_sums())
+        view.close()
     srv.close_tenant(t)
     if results is not None:
         results[key] = outs
@@ -140,3 +148,54 @@ def test_learned_tenant_matches_direct_learned_estimate():
         v.slide()
         np.testing.assert_array_equal(v.estimate_learned(mlp, d_aips).cpu().numpy(), want)
     srv.close()
+
+
+def _oracle_run(cfg, aips, slices):
+    o = oracle.Oracle(cfg.layout, k=cfg.k, Z=cfg.num_bdr, b=cfg.log2_g, seed=cfg.seed)
+    outs = []
+    for s in slices:
+        o.scan(s.numpy().view(np.uint32).reshape(-1, 2))
+        o.slide()
+        outs.append(o.estimate(aips))
+    return outs, o.registers(), o.pool_sums()
+
+
+def _assert_close_to_oracle(got, want, tag):
+    got = got.astype(np.float64)
+    err = np.abs(got - want) / np.maximum(np.abs(want), 1.0)
+    assert err.max() <= 1e-6, (tag, float(err.max()), int(err.argmax()))
+
+
+@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+def test_served_results_match_oracle_alone_and_in_mix(layout):
+    """Each tenant's per-slice estimates, served alone and in a mix of three
+    concurrent tenants, against the CPU oracle run on the same slices; the
+    slice sizes are log-uniform with one empty slice and one at the
+    tenant's capacity; the final registers and pool sums bit for bit."""
+    from paper_1810_13132_gb300 import Server
+    works = {i: _workload(400 + i) for i in range(3)}
+    gen = traffic.ZipfTraffic(3000, 1.1, 5000, 5, seed=499)
+    works[0][1][6] = torch.from_numpy(gen.next_slice(300_000).view(np.int32)).pin_memory()
+    assert works[0][1][3].numel() == 0 and works[0][1][6].numel() == 2 * 300_000
+    cfg = _cfg(layout)
+    srv = Server(budget_bytes=8 << 30)
+    alone, alone_state = {}, {}
+    for i in works:
+        alone[i] = _run_tenant(srv, cfg, *works[i], states=alone_state, key=i)
+    mixed, mixed_state = {}, {}
+    th = [threading.Thread(target=_run_tenant, args=(srv, cfg, *works[i]),
+                           kwargs=dict(results=mixed, key=i, states=mixed_state)) for i in works]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    srv.close()
+    for i in works:
+        want, reg, sums = _oracle_run(cfg, *works[i])
+        assert len(alone[i]) == len(mixed[i]) == len(want)
+        for t, (a, m, w) in enumerate(zip(alone[i], mixed[i], want)):
+            _assert_close_to_oracle(a, w, (i, t, "alone"))
+            _assert_close_to_oracle(m, w, (i, t, "mix"))
+        for st in (alone_state[i], mixed_state[i]):
+            np.testing.assert_array_equal(st[0], reg)
+            assert st[1] == sums
