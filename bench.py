@@ -480,10 +480,13 @@ def run_extras(a, wl, slices, d_slices, plan, d_aips, peak):
     the trace step in the gsmall layout, batched estimation of 4M hosts and
     a short serving run."""
     out = {}
-    try:
-        out["gsmall"] = _trace_layout_step(a, wl, d_slices, plan, d_aips, "gsmall", peak)
-    except Exception as e:  # reported, never fatal to the main line
-        out["gsmall"] = {"error": repr(e)}
+    for key, layout, mode in (("gsmall", "gsmall", "direct"),
+                              ("bucketed_scan_gfast", "gfast", "bucketed"),
+                              ("bucketed_scan_gsmall", "gsmall", "bucketed")):
+        try:
+            out[key] = _trace_layout_step(a, wl, d_slices, plan, d_aips, layout, peak, mode)
+        except Exception as e:  # reported, never fatal to the main line
+            out[key] = {"error": repr(e)}
     try:
         out["batched"] = batched_core(a)
     except Exception as e:
@@ -495,13 +498,15 @@ def run_extras(a, wl, slices, d_slices, plan, d_aips, peak):
     return out
 
 
-def _trace_layout_step(a, wl, d_slices, plan, d_aips, layout, peak):
-    """The trace step (scan + slide + planned estimate) in another layout, on
-    the same device-resident slices and host-list plan, timed per kernel."""
+def _trace_layout_step(a, wl, d_slices, plan, d_aips, layout, peak, scan_mode="direct"):
+    """The trace step (scan + slide + planned estimate) in another layout or
+    with another scan kernel, on the same device-resident slices and
+    host-list plan, timed per kernel."""
     import torch
     from paper_1810_13132_gb300 import Config, Vbdr
     N, H = wl["n_pairs"], wl["n_hosts"]
     v = Vbdr(Config(k=wl["k"], num_bdr=wl["Z"], log2_g=wl["log2_g"], layout=layout, seed=SEED))
+    v.set_scan_mode(scan_mode)
     out = torch.empty(H, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     nsl = len(d_slices)
@@ -526,7 +531,8 @@ def _trace_layout_step(a, wl, d_slices, plan, d_aips, layout, peak):
     tot = evs[0][0].elapsed_time(evs[-1][3]) / a.steps
     sb = _slide_bytes(layout, wl["Z"], v.words)
     v.close()
-    return {"layout": layout, "value": round(N / (tot * 1e-3) / 1e9, 3), "unit": "G pairs/s",
+    return {"layout": layout, "scan_mode": scan_mode,
+            "value": round(N / (tot * 1e-3) / 1e9, 3), "unit": "G pairs/s",
             "ms_per_step": round(tot, 4), "scan_ms": round(sc, 4),
             "scan_gpairs_per_s": round(N / (sc * 1e-3) / 1e9, 3),
             "scan_hbm_frac": round(8 * N / (sc * 1e-3) / 1e9 / peak, 4),

@@ -260,6 +260,22 @@ VBDR_API int vbdr_estimate_registers_noalloc(const uint8_t *d_reg, uint64_t num_
                                              const uint32_t *d_aips, uint64_t n_hosts,
                                              float *d_out, void *stream);
 
+/* Scan kernels.  VBDR_SCAN_DIRECT (the default): each pair's update word
+ * is tested with one cached load and changed with one atomic only when the
+ * update changes it (Alg. 7 / Alg. 9 / Alg. 4).  VBDR_SCAN_BUCKETED: for
+ * slices of at least 2^18 pairs, the pairs are routed as 4-byte records to
+ * the 2^16-BDR tile of the pool that owns them and every tile applies its
+ * records in shared memory, writing the state once per scan call (gfast
+ * and gsmall only, g <= 512, Z <= 2^27).  Both give the same state bit for
+ * bit; the direct kernel is faster on this GPU (the bucketed one is kept
+ * for measurement).  Selecting the bucketed scan allocates its buffers once
+ * (about 64 MiB for a 2^24 pool) after synchronising the device, so select
+ * it before any stream capture.  Errors: VBDR_EINVAL (unknown mode, or
+ * bucketed on a layout or size it does not serve), VBDR_ENOMEM. */
+#define VBDR_SCAN_DIRECT 0
+#define VBDR_SCAN_BUCKETED 1
+VBDR_API int vbdr_set_scan_mode(vbdr_t h, int mode);
+
 /* ---- several GPUs --------------------------------------------------------
  * The paper's scan is data parallel over pairs and its slide over BDRs
  * (Sec. 4.2): every update ORs a bsLBP1 bit (Alg. 7), zeroes a DR (Alg. 9)

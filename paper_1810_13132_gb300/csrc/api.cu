@@ -48,7 +48,8 @@ struct vbdr {
   uint64_t est_cap;
   uint16_t *d_feat;     // feature rows of the learned estimate [feat_cap][48]
   uint64_t feat_cap;
-  vbk::BucketDev bk;    // record buckets of the bucketed scan (bk.recs null: not used)
+  vbk::BucketDev bk;    // buffers of the bucketed scan (allocated when it is selected)
+  int scan_mode;        // VBDR_SCAN_DIRECT (default) or VBDR_SCAN_BUCKETED
 };
 
 // A host list's estimate plan (plan.cu): device arrays plus the handle
@@ -128,8 +129,18 @@ void fill_est_const(const Dims &d, EstConst *c) {
   c->pc_Z = Z / kPcsaPhi;
 }
 
+// VBDR_VERBOSE=1 names on stderr the CUDA error behind a VBDR_ECUDA.
+void report_cuda(cudaError_t e) {
+  static const bool verbose = [] {
+    const char *v = std::getenv("VBDR_VERBOSE");
+    return v && v[0] == '1';
+  }();
+  if (verbose) std::fprintf(stderr, "vbdr: CUDA error %d (%s)\n", (int)e, cudaGetErrorString(e));
+}
+
 int fail_cuda(vbdr *h, cudaError_t e) {
   if (e != cudaSuccess) {
+    report_cuda(e);
     h->sticky = VBDR_ECUDA;
     return VBDR_ECUDA;
   }
@@ -169,6 +180,7 @@ void free_state(vbdr *h) {
   cudaFree(h->d_feat);
   cudaFree(h->bk.recs);
   cudaFree(h->bk.fill);
+  cudaFree(h->bk.lb);
 }
 
 // Slices of at least this many pairs take the bucketed scan (bucket.cu); its
@@ -176,23 +188,10 @@ void free_state(vbdr *h) {
 // slices do not repay.
 constexpr uint64_t kBucketMinPairs = 1ull << 18;
 
-// Record capacity of the bucketed scan: at most 2^24 records (64 MiB, so
-// that one pass's records stay in L2), at least 2^20, else one 2^16-record
-// bucket per tile; a pass routes two thirds of the capacity, which leaves
-// every bucket 50% headroom over its mean load.
-void bucket_sizes(const Dims &d, uint32_t *ntiles, uint32_t *cap, uint64_t *pass_pairs) {
-  const uint64_t nt = (d.Z + vbk::kBucketTile - 1) / vbk::kBucketTile;
-  uint64_t total = nt * vbk::kBucketTile;
-  total = std::min<uint64_t>(std::max<uint64_t>(total, 1ull << 20), 1ull << 24);
-  *ntiles = (uint32_t)nt;
-  *cap = (uint32_t)(total / nt);
-  *pass_pairs = (total * 2 / 3) & ~((1ull << 14) - 1);
-}
-
 // The scan of n pairs (n_dev: device-side count up to n, for graphs).
 cudaError_t scan_any(vbdr *h, const uint32_t *pairs, uint64_t n, cudaStream_t st,
                      const uint64_t *n_dev = nullptr) {
-  if (h->bk.recs && n >= kBucketMinPairs)
+  if (h->scan_mode == VBDR_SCAN_BUCKETED && h->bk.recs && n >= kBucketMinPairs)
     return vbk::launch_scan_bucketed(h->d, h->s, h->bk, h->layout, pairs, n, st, n_dev);
   return vbk::launch_scan(h->d, h->s, h->layout, pairs, n, st, n_dev);
 }
@@ -279,12 +278,6 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->s.lnv, vbk::kLnTab * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.sums, vbk::kSums * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&h->s.check, sizeof(unsigned int));
-  if (e == cudaSuccess && vbk::bucket_scan_applies(d, h->layout)) {
-    bucket_sizes(d, &h->bk.ntiles, &h->bk.cap, &h->bk.pass_pairs);
-    e = cudaMalloc(&h->bk.recs, (size_t)h->bk.ntiles * h->bk.cap * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&h->bk.fill, (size_t)h->bk.ntiles * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(h->bk.fill, 0, (size_t)h->bk.ntiles * sizeof(uint32_t));
-  }
   if (e == cudaSuccess) {
     double lnv[vbk::kLnTab];
     lnv[0] = 0.0;
@@ -295,6 +288,7 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   h->est_cfg = vbk::kEstCandidates[0];
   if (e != cudaSuccess) {
     cudaGetLastError();
+    report_cuda(e);
     free_state(h);
     delete h;
     return e == cudaErrorMemoryAllocation ? VBDR_ENOMEM : VBDR_ECUDA;
@@ -303,6 +297,7 @@ int vbdr_create(const vbdr_config *cfg, vbdr_t *out) {
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
+    report_cuda(e);
     free_state(h);
     delete h;
     return VBDR_ECUDA;
@@ -316,6 +311,39 @@ int vbdr_destroy(vbdr_t h) {
   cudaDeviceSynchronize();
   free_state(h);
   delete h;
+  return VBDR_OK;
+}
+
+int vbdr_set_scan_mode(vbdr_t h, int mode) {
+  if (!h) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (mode == VBDR_SCAN_DIRECT) {
+    h->scan_mode = mode;
+    return VBDR_OK;
+  }
+  if (mode != VBDR_SCAN_BUCKETED) return VBDR_EINVAL;
+  if (!vbk::bucket_scan_applies(h->d, h->layout)) return VBDR_EINVAL;
+  if (!h->bk.recs) {  // the buffers, once per handle
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    vbk::BucketDev bk = {};
+    vbk::bucket_layout(h->d.Z, sms, &bk);
+    const size_t regions = (size_t)bk.ncta * bk.ntiles;
+    e = cudaMalloc(&bk.recs, regions * bk.cap * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&bk.fill, regions * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&bk.lb, (size_t)bk.ntiles << vbk::kBucketTileLog2);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(bk.recs);
+      cudaFree(bk.fill);
+      cudaFree(bk.lb);
+      return e == cudaErrorMemoryAllocation ? VBDR_ENOMEM : fail_cuda(h, e);
+    }
+    h->bk = bk;
+  }
+  h->scan_mode = mode;
   return VBDR_OK;
 }
 
@@ -940,6 +968,7 @@ int vbdr_plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n, vbdr_plan_t *
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(pd.goff, goff.data(), (ngroups + 1) * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = vbk::launch_plan_fill(d, h->s, pd, st);
+  if (e == cudaSuccess) e = vbk::launch_plan_sort(pd, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(e);
   cudaFree(pd.counts);

@@ -118,6 +118,91 @@ __global__ void __launch_bounds__(kBuildThreads)
     for (unsigned long long q = goff[c] + cur[c]; q < goff[c + 1]; ++q) p.entries[q] = kPlanPad;
 }
 
+// Building, pass 3: the order of a group's staged entries (the first
+// kEntCap) is chosen so that the 32 entries one warp instruction takes --
+// lane L holds the uint4 at position 32 r + L, so for component j the
+// entries at 128 r + 4 L + j -- read the register chunk in 32 different
+// shared-memory banks wherever the group allows it: entry positions with
+// (pos >> 2) mod 32 = b are given to entries whose register byte lies in
+// bank b, in order; the entries left over fill the remaining positions.
+// The sums are order independent, so the estimates do not change.
+constexpr uint32_t kSortThreads = 1024;
+constexpr size_t kSortSmem = kEntCap * (3 * sizeof(uint32_t) + sizeof(uint16_t));
+__global__ void __launch_bounds__(kSortThreads)
+    plan_sort_kernel(PlanDev p) {
+  extern __shared__ uint32_t sort_smem[];  // kSortSmem bytes
+  uint32_t *in = sort_smem, *out = sort_smem + kEntCap, *hole = sort_smem + 2 * kEntCap;
+  uint16_t *rank = reinterpret_cast<uint16_t *>(sort_smem + 3 * kEntCap);
+  __shared__ uint32_t cnt[32], cap[32], warp_holes[32], n_left;
+  const uint32_t blk = blockIdx.x, tid = threadIdx.x;
+  const uint32_t lane = tid & 31u, warp = tid >> 5;
+  const unsigned long long *goff = p.goff + (uint64_t)blk * p.nchunks;
+  for (uint32_t c = 0; c < p.nchunks; ++c) {
+    const unsigned long long q0 = goff[c], len = goff[c + 1] - q0;
+    const uint32_t P = len < kEntCap ? (uint32_t)len : kEntCap;  // a multiple of 4
+    if (P == 0) continue;
+    if (tid < 32) cnt[tid] = 0;
+    if (tid == 0) n_left = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < P; i += kSortThreads) {
+      const uint32_t e = p.entries[q0 + i];
+      in[i] = e;
+      rank[i] = (uint16_t)atomicAdd(&cnt[((e & (kChunkBytes - 1)) >> 2) & 31u], 1u);
+    }
+    // positions of bank b: 128 r + 4 b + j < P
+    if (tid < 32) {
+      const uint32_t full = P / 128, rest = P % 128;
+      const uint32_t lo = 4 * tid;
+      cap[tid] = 4 * full + (rest > lo ? min(rest - lo, 4u) : 0u);
+    }
+    for (uint32_t i = tid; i < P; i += kSortThreads) out[i] = 0xffffffffu;
+    __syncthreads();
+    for (uint32_t i = tid; i < P; i += kSortThreads) {
+      const uint32_t e = in[i], b = ((e & (kChunkBytes - 1)) >> 2) & 31u, k = rank[i];
+      if (k < cap[b]) out[128 * (k >> 2) + 4 * b + (k & 3)] = e;
+    }
+    __syncthreads();
+    // the free positions, in increasing order (block-wide count of each
+    // thread's run of 4 positions)
+    uint32_t mine = 0;
+    for (uint32_t j = 0; j < 4; ++j) {
+      const uint32_t pos = 4 * tid + j;
+      mine += pos < P && out[pos] == 0xffffffffu;
+    }
+    uint32_t x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) warp_holes[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = warp_holes[lane], v = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= (uint32_t)o) v += y;
+      }
+      warp_holes[lane] = v - w;  // exclusive prefix over warps
+    }
+    __syncthreads();
+    uint32_t h = warp_holes[warp] + x - mine;
+    for (uint32_t j = 0; j < 4; ++j) {
+      const uint32_t pos = 4 * tid + j;
+      if (pos < P && out[pos] == 0xffffffffu) hole[h++] = pos;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < P; i += kSortThreads) {
+      const uint32_t e = in[i], b = ((e & (kChunkBytes - 1)) >> 2) & 31u;
+      if (rank[i] >= cap[b]) out[hole[atomicAdd(&n_left, 1u)]] = e;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < P; i += kSortThreads) p.entries[q0 + i] = out[i];
+    __syncthreads();
+  }
+}
+
 // Shared memory of the planned estimate.
 constexpr uint32_t kAccRow = kPlanMaxHB + 1;  // + the spare slot of padding entries
 struct PlanSmem {
@@ -251,6 +336,15 @@ cudaError_t launch_plan_count(const Dims &d, const DevState &s, const PlanDev &p
 cudaError_t launch_plan_fill(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st) {
   if (p.NB == 0) return cudaSuccess;
   plan_fill_kernel<<<p.NB, kBuildThreads, p.nchunks * sizeof(uint32_t), st>>>(d, s, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plan_sort(const PlanDev &p, cudaStream_t st) {
+  if (p.NB == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(plan_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kSortSmem);
+  if (e != cudaSuccess) return e;
+  plan_sort_kernel<<<p.NB, kSortThreads, kSortSmem, st>>>(p);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,8 @@
 // deadline); no kernel here waits on anything.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <mutex>
@@ -75,7 +77,13 @@ struct vbdr_server {
 
 namespace {
 
-int cuda_rc(cudaError_t e) { return e == cudaSuccess ? VBDR_OK : VBDR_ECUDA; }
+int cuda_rc(cudaError_t e) {
+  if (e == cudaSuccess) return VBDR_OK;
+  const char *v = std::getenv("VBDR_VERBOSE");  // name the failing CUDA error
+  if (v && v[0] == '1') std::fprintf(stderr, "vbdr server: CUDA error %d (%s)\n", (int)e,
+                                     cudaGetErrorString(e));
+  return VBDR_ECUDA;
+}
 
 void free_tenant(Tenant &t) {
   if (t.compute) cudaStreamSynchronize(t.compute);
@@ -103,7 +111,7 @@ void free_tenant(Tenant &t) {
 int capture_slot(Tenant &t, Slot &s, vbdr_mlp_t mlp) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(t.compute, cudaStreamCaptureModeRelaxed);
-  if (e != cudaSuccess) return VBDR_ECUDA;
+  if (e != cudaSuccess) return cuda_rc(e);
   int rc = vbdr_scan_slice_devn(t.h, s.d_pairs, s.d_n, t.max_pairs, t.compute);
   if (rc == VBDR_OK) rc = vbdr_slide(t.h, t.compute);
   if (rc == VBDR_OK)
@@ -115,7 +123,7 @@ int capture_slot(Tenant &t, Slot &s, vbdr_mlp_t mlp) {
   e = cudaStreamEndCapture(t.compute, &g);
   if (rc != VBDR_OK || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
-    return rc != VBDR_OK ? rc : VBDR_ECUDA;
+    return rc != VBDR_OK ? rc : cuda_rc(e);
   }
   e = cudaGraphInstantiate(&s.exec, g, 0);
   cudaGraphDestroy(g);
@@ -139,10 +147,6 @@ uint64_t vbdr_server_tenant_bytes(const vbdr_config *cfg, uint64_t max_pairs, ui
                    (cfg->layout == VBDR_SERIAL ? Zs : 0) +
                    (cfg->layout == VBDR_GSMALL ? Zs : 0);  // PCSA statistics
   bytes += 64ull << 10;                                // tables, sums
-  if (cfg->layout != VBDR_SERIAL) {                    // record buckets of the bucketed scan
-    const uint64_t nt = (cfg->num_bdr + 65535) / 65536;
-    bytes += 4 * std::min<uint64_t>(std::max<uint64_t>(nt * 65536, 1ull << 20), 1ull << 24) + 4 * nt;
-  }
   bytes += 2 * (max_pairs * 8 + 8 + n_hosts * 4);      // staging slots
   bytes += n_hosts * 4;                                // host list
   return bytes;
@@ -217,7 +221,7 @@ int vbdr_server_open(vbdr_server_t s, const vbdr_config *cfg, uint64_t max_pairs
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
-    rc = e == cudaErrorMemoryAllocation ? VBDR_ENOMEM : VBDR_ECUDA;
+    rc = e == cudaErrorMemoryAllocation ? VBDR_ENOMEM : cuda_rc(e);
   }
   // The estimate call refuses to run before a first slide, so close one empty
   // slice eagerly before capturing: on the fresh state (every DR saturated,

@@ -233,21 +233,26 @@ cudaError_t launch_estimate_alt(const Dims &d, const DevState &s, const EstConst
                                 cudaStream_t st, EstLaunch cfg);
 
 // ----- bucketed scan (bucket.cu) -----
-// Pool tiles of 2^16 BDRs; a slice's pairs become 4-byte records
-// (pidx mod 2^16) << 5 | (LBP1 - 1) in their tile's bucket, then each tile
-// applies its bucket in shared memory.  Records of one tile occupy
-// recs[t cap, t cap + min(fill[t], cap)).
+// Pool tiles of 2^16 BDRs.  Each pass, route CTA c appends the records
+// (pidx mod 2^16) << 3 | (LBP1 - 1) of tile t to its own region
+// recs[(c ntiles + t) cap ...] and publishes the count in fill[c ntiles + t];
+// one apply CTA per tile then ORs them into the tile's bytes (lb between
+// passes: one byte per BDR, bit r = LBP1 r + 1 seen).
 constexpr uint32_t kBucketTileLog2 = 16;
 constexpr uint32_t kBucketTile = 1u << kBucketTileLog2;
 constexpr uint32_t kMaxBucketTiles = 2048;  // Z <= 2^27
 struct BucketDev {
-  uint32_t *recs;       // [ntiles][cap]
-  uint32_t *fill;       // [ntiles], zero between passes
+  uint32_t *recs;       // [ncta][ntiles][cap]
+  uint32_t *fill;       // [ncta][ntiles]
+  uint8_t *lb;          // [ntiles * 2^16]
   uint32_t ntiles;
-  uint32_t cap;         // records per bucket
+  uint32_t ncta;        // route grid
+  uint32_t cap;         // records per CTA region of a tile
   uint64_t pass_pairs;  // pairs routed per pass (a multiple of the route batch)
 };
 bool bucket_scan_applies(const Dims &d, int layout);
+void bucket_layout(uint64_t Z, int sms, BucketDev *bk);
+uint64_t bucket_bytes(const BucketDev &bk);
 cudaError_t launch_scan_bucketed(const Dims &d, const DevState &s, const BucketDev &bk, int layout,
                                  const uint32_t *pairs, uint64_t n, cudaStream_t st,
                                  const uint64_t *n_dev = nullptr);
@@ -286,6 +291,7 @@ struct PlanDev {
 };
 cudaError_t launch_plan_count(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st);
 cudaError_t launch_plan_fill(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st);
+cudaError_t launch_plan_sort(const PlanDev &p, cudaStream_t st);
 cudaError_t launch_planned_estimate(const Dims &d, const DevState &s, const EstConst &c,
                                    const PlanDev &p, float *out, cudaStream_t st);
 

@@ -96,6 +96,7 @@ _SIGS = {
     "vbdr_state_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(_U64)]),
     "vbdr_save": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
     "vbdr_load": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
+    "vbdr_set_scan_mode": (ctypes.c_int, [_VP, ctypes.c_int]),
     "vbdr_state_pointers": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_U64),
                                            ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "vbdr_route_records": (ctypes.c_int, [_VP, _VP, _U64, _U32, _VP, _U64, _VP, _VP]),
@@ -214,6 +215,12 @@ class Vbdr:
             self.close()
         except Exception:
             pass
+
+    SCAN_MODES = {"direct": 0, "bucketed": 1}
+
+    def set_scan_mode(self, mode: str) -> None:
+        """"direct" (default) or "bucketed" scan kernels (same state)."""
+        _check("vbdr_set_scan_mode", self._L.vbdr_set_scan_mode(self._h, self.SCAN_MODES[mode]))
 
     # -- the hot path ----------------------------------------------------------
     def scan(self, pairs, stream=None) -> None:

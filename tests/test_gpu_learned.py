@@ -168,3 +168,35 @@ def test_training_gain_and_fused_estimate(data):
     mre_f = np.mean(np.abs(fused[live] - truth[live]) / truth[live])
     mre_p = np.mean(np.abs(p[live] - truth[live]) / truth[live])
     assert mre_f < 0.6 * mre_p, (mre_f, mre_p)
+
+
+def test_feature_calls_check_alignment_and_g():
+    """The feature rows are written with 8- and 16-byte stores, so d_X must be
+    16-byte aligned; the histogram counts fit g <= 512 only."""
+    from paper_1810_13132_gb300 import Config, Mlp, Vbdr, VbdrError
+    from paper_1810_13132_gb300.vbdr import _stream_ptr
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    v = Vbdr(Config(k=3, num_bdr=1 << 16, log2_g=8))
+    v.scan(torch.zeros((1024, 2), dtype=torch.int32, device="cuda"))
+    v.slide()
+    aips = torch.arange(64, dtype=torch.int32, device="cuda")
+    X = torch.empty((64 * 48 + 8,), dtype=torch.bfloat16, device="cuda")
+    plain = torch.empty(64, dtype=torch.float32, device="cuda")
+    rc = v._L.vbdr_features(v._h, aips.data_ptr(), 64, X.data_ptr() + 8, plain.data_ptr(),
+                            _stream_ptr(None))
+    assert rc == -1  # 8-byte aligned rows are refused
+    rc = v._L.vbdr_features(v._h, aips.data_ptr(), 64, X.data_ptr(), plain.data_ptr(),
+                            _stream_ptr(None))
+    assert rc == 0
+    big = Vbdr(Config(k=3, num_bdr=1 << 16, log2_g=11))
+    big.scan(torch.zeros((1024, 2), dtype=torch.int32, device="cuda"))
+    big.slide()
+    with pytest.raises(VbdrError) as e:
+        big.features(aips)
+    assert e.value.code == -4
+    with pytest.raises(VbdrError) as e:
+        big.estimate_learned(Mlp(seed=2), aips)
+    assert e.value.code == -4
+    torch.cuda.synchronize()

@@ -29,10 +29,11 @@ def _dev(a: np.ndarray):
     return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
 
 
-def _make(layout, k, Z, b, b_min=None, group_rule=0, seed=SEED):
+def _make(layout, k, Z, b, b_min=None, group_rule=0, seed=SEED, scan_mode="direct"):
     from paper_1810_13132_gb300 import Config, Vbdr
     v = Vbdr(Config(k=k, num_bdr=Z, log2_g=b, layout=layout, seed=seed,
                     log2_g_min=b_min or 0, group_rule=group_rule))
+    v.set_scan_mode(scan_mode)
     o = oracle.Oracle(layout, k=k, Z=Z, b=b, seed=seed, b_min=b_min,
                       group_rule=group_rule)
     assert v.R == o.R
@@ -61,8 +62,8 @@ def _compare_estimates(v, o, aips):
 
 
 def _run(layout, k, Z, b, slices, aips, b_min=None, group_rule=0, every=True,
-         split=1):
-    v, o = _make(layout, k, Z, b, b_min, group_rule)
+         split=1, scan_mode="direct"):
+    v, o = _make(layout, k, Z, b, b_min, group_rule, scan_mode=scan_mode)
     for t, s in enumerate(slices):
         if split == 1:
             v.scan(_dev(s))
@@ -227,9 +228,18 @@ def test_all_layouts_agree_on_gpu():
 
 
 # ------------------------------------------------------ bucketed scan path
-# Slices of at least 2^18 pairs (gfast, gsmall) take the bucketed scan: pairs
-# become records in per-tile buckets that each pool tile applies in shared
-# memory.  These cases stress what is specific to it.
+# With the bucketed scan selected, slices of at least 2^18 pairs (gfast,
+# gsmall) become records in per-tile buckets that each pool tile applies in
+# shared memory.  These cases stress what is specific to it.
+
+@pytest.mark.parametrize("layout", ["gfast", "gsmall"])
+def test_bucketed_scan_trace_shape_downscaled(layout):
+    """The trace-shaped workload at 1/64 (1M pairs per slice, two passes'
+    worth of records on a 2^18 pool), state after every slice."""
+    gen = traffic.ZipfTraffic(16384, 1.05, 2_000_000 // 64, 30, seed=122, repeat_frac=0.10)
+    slices = [gen.next_slice(1 << 20) for _ in range(6)]
+    _run(layout, 30, 1 << 18, 8, slices, gen.aips, scan_mode="bucketed")
+
 
 @pytest.mark.parametrize("layout", ["gfast", "gsmall"])
 def test_bucketed_scan_bucket_overflow(layout):
@@ -239,7 +249,7 @@ def test_bucketed_scan_bucket_overflow(layout):
     rng = np.random.default_rng(120)
     aip = np.array([0x01020304], dtype=np.uint32)
     slices = [traffic.uniform_pairs(rng, 2_000_001, aip) for _ in range(3)]
-    _run(layout, 3, 1 << 20, 4, slices, aip)
+    _run(layout, 3, 1 << 20, 4, slices, aip, scan_mode="bucketed")
 
 
 @pytest.mark.parametrize("layout", ["gfast", "gsmall"])
@@ -251,8 +261,10 @@ def test_bucketed_scan_threshold_split_and_mixed_g(layout):
     aips = traffic.distinct_u32(rng, 6000)
     sizes = [(1 << 18) - 2, 1 << 18, 600_001, (1 << 18) + 1]
     slices = [traffic.uniform_pairs(rng, n, aips) for n in sizes]
-    _run(layout, 7, (3 << 16) + 77, 6, slices[:2], aips, b_min=6, group_rule=1)
-    _run(layout, 7, (3 << 16) + 77, 6, slices[2:], aips, b_min=6, group_rule=1, split=2)
+    _run(layout, 7, (3 << 16) + 77, 6, slices[:2], aips, b_min=6, group_rule=1,
+         scan_mode="bucketed")
+    _run(layout, 7, (3 << 16) + 77, 6, slices[2:], aips, b_min=6, group_rule=1, split=2,
+         scan_mode="bucketed")
 
 
 # --------------------------------------------------------- host-buffer path
@@ -292,6 +304,15 @@ def test_estimate_before_slide_is_an_order_error():
     assert e.value.code == -5
 
 
+def test_scan_mode_selection():
+    from paper_1810_13132_gb300 import Config, Vbdr, VbdrError
+    v = Vbdr(Config(k=3, num_bdr=4096, log2_g=5, layout="serial"))
+    with pytest.raises(VbdrError) as e:
+        v.set_scan_mode("bucketed")  # the bucketed scan serves gfast and gsmall
+    assert e.value.code == -1
+    v.set_scan_mode("direct")
+
+
 def test_misaligned_pairs_rejected():
     from paper_1810_13132_gb300 import Config, Vbdr, VbdrError
     v = Vbdr(Config(k=3, num_bdr=4096, log2_g=5))
@@ -303,8 +324,10 @@ def test_misaligned_pairs_rejected():
 
 # ------------------------------------------------ full-size trace, sampled
 
-@pytest.mark.parametrize("layout", ["gfast", "gsmall", "serial"])
-def test_trace_full_size_two_slices(layout):
+@pytest.mark.parametrize("layout,scan_mode", [("gfast", "direct"), ("gsmall", "direct"),
+                                              ("serial", "direct"), ("gfast", "bucketed"),
+                                              ("gsmall", "bucketed")])
+def test_trace_full_size_two_slices(layout, scan_mode):
     """The trace configuration at full size (N = 64M pairs per slice, 1M
     hosts, Z = 2^24, g = 256, k = 30, 10% repeats), two slices in the launch
     configuration the benchmark uses: state bit-exact after both slides and
@@ -312,7 +335,7 @@ def test_trace_full_size_two_slices(layout):
     cfg = traffic.TRACE
     gen = traffic.ZipfTraffic(cfg["n_hosts"], cfg["zipf_s"], cfg["c_max"], cfg["k"],
                               seed=111, repeat_frac=cfg["repeat_frac"])
-    v, o = _make(layout, cfg["k"], cfg["Z"], cfg["log2_g"])
+    v, o = _make(layout, cfg["k"], cfg["Z"], cfg["log2_g"], scan_mode=scan_mode)
     for t in range(2):
         s = gen.next_slice(cfg["n_pairs"])
         v.scan(_dev(s))
