@@ -312,9 +312,34 @@ def run_ours(a):
             v.estimate_learned(mlp, d_aips, out=d_out2)
         ev[3].record(stream)
         torch.cuda.synchronize()
-        learned = {"estimate_ms_plain": round(ev[0].elapsed_time(ev[1]) / a.steps, 4),
-                   "estimate_ms_learned": round(ev[2].elapsed_time(ev[3]) / a.steps, 4),
+        learned = {"estimate_ms_plain_gather": round(ev[0].elapsed_time(ev[1]) / a.steps, 4),
+                   "estimate_ms_learned_gather": round(ev[2].elapsed_time(ev[3]) / a.steps, 4),
                    "weights": os.path.relpath(wpath, ROOT)}
+        # the same correction through a host-list plan (built once, like the
+        # plain one): the step's learned estimate
+        lplan = v.plan(d_aips, learned=True)
+        d_out3 = torch.empty(H, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            v.estimate_learned_planned(mlp, lplan, out=d_out3)
+        torch.cuda.synchronize()
+        same_l = bool(torch.equal(d_out3.view(torch.int32), d_out2.view(torch.int32)))
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for _ in range(a.steps):
+            v.estimate_learned_planned(mlp, lplan, out=d_out3)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        lplan.status()
+        lp_ms = l0.elapsed_time(l1) / a.steps
+        plain_ms = statistics.mean(est_ms)
+        learned.update({
+            "estimate_ms_learned_planned": round(lp_ms, 4),
+            "estimate_ms_plain_planned": round(plain_ms, 4),
+            "learned_planned_equals_gather": same_l,
+            "step_ms_learned": round(statistics.mean(scan_ms) + statistics.mean(slide_ms) + lp_ms, 4),
+            "step_ms_plain": round(ms_step, 4),
+            "learned_plan": lplan.info()})
+        lplan.close()
 
     # accuracy on the state the timed steps left (window = union of the
     # distinct slices once k >= N_DISTINCT_SLICES slices have been scanned)

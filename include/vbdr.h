@@ -222,6 +222,13 @@ VBDR_API int vbdr_plan_status(vbdr_plan_t p);
  * configuration or device), VBDR_EORDER (no slide yet), VBDR_ECUDA. */
 VBDR_API int vbdr_estimate_planned(vbdr_t h, vbdr_plan_t p, float *d_out, void *stream);
 
+/* A plan as vbdr_plan_create builds it, with blocks of at most 3300 hosts:
+ * what vbdr_estimate_learned_planned needs (its per-host register
+ * histograms share a block's shared memory); vbdr_estimate_planned accepts
+ * it too.  Errors: as vbdr_plan_create. */
+VBDR_API int vbdr_plan_create_learned(vbdr_t h, const uint32_t *d_aips, uint64_t n,
+                                      vbdr_plan_t *out, void *stream);
+
 /* vbdr_estimate_planned with the estimates written to HOST memory h_out
  * (valid once the stream has passed the call), through a device buffer owned
  * by the handle.  Errors: as vbdr_estimate_planned, plus VBDR_ENOMEM. */
@@ -435,6 +442,17 @@ VBDR_API int vbdr_features(vbdr_t h, const uint32_t *d_aips, uint64_t n_hosts, u
  * plus VBDR_ERANGE (largest g of the handle above 512, as vbdr_features). */
 VBDR_API int vbdr_estimate_learned(vbdr_t h, vbdr_mlp_t m, const uint32_t *d_aips,
                                    uint64_t n_hosts, float *d_out, void *stream);
+
+/* vbdr_estimate_learned for the hosts of a plan made by
+ * vbdr_plan_create_learned: the same feature rows and the same corrected
+ * estimates, bit for bit, with the registers read chunk by chunk through the
+ * plan instead of gathered (Alg. 5 with Alg. 3 as in vbdr_estimate_planned).
+ * d_out: device, n_hosts floats, 4-byte aligned, plan order.  Errors:
+ * VBDR_EINVAL (NULL, misaligned, plan of another configuration or built by
+ * vbdr_plan_create), VBDR_ERANGE (a g above 512), VBDR_EORDER, VBDR_ENOMEM,
+ * VBDR_ECUDA; a bounded wait that expired shows in vbdr_plan_status. */
+VBDR_API int vbdr_estimate_learned_planned(vbdr_t h, vbdr_mlp_t m, vbdr_plan_t p, float *d_out,
+                                           void *stream);
 
 /* ---- streaming service ----
  * A server runs many VBDR instances ("tenants", e.g. one per monitored

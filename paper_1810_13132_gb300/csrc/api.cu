@@ -895,9 +895,32 @@ int vbdr_set_registers(vbdr_t h, const uint8_t *d_reg, const uint8_t *d_pcsa, vo
 
 /* ---------------------------------------------------------------- plans */
 
+}  // extern "C"
+
+namespace {
+int plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n, uint32_t max_hb, vbdr_plan_t *out,
+                void *stream);
+}  // namespace
+
+extern "C" {
+
 int vbdr_plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n, vbdr_plan_t *out,
                      void *stream) {
   NvtxRange nvtx("vbdr_plan_create");
+  return plan_create(h, d_aips, n, vbk::kPlanMaxHB, out, stream);
+}
+
+int vbdr_plan_create_learned(vbdr_t h, const uint32_t *d_aips, uint64_t n, vbdr_plan_t *out,
+                             void *stream) {
+  NvtxRange nvtx("vbdr_plan_create_learned");
+  return plan_create(h, d_aips, n, vbk::kLearnMaxHB, out, stream);
+}
+
+}  // extern "C"
+
+namespace {
+int plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n, uint32_t max_hb, vbdr_plan_t *out,
+                void *stream) {
   if (!h || !out) return VBDR_EINVAL;
   *out = nullptr;
   if (h->sticky) return h->sticky;
@@ -909,8 +932,8 @@ int vbdr_plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n, vbdr_plan_t *
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   if (sms < 1) sms = 1;
-  // blocks of at most kPlanMaxHB hosts, a whole number of waves of one block per SM
-  const uint64_t per_wave = (uint64_t)sms * vbk::kPlanMaxHB;
+  // blocks of at most max_hb hosts, a whole number of waves of one block per SM
+  const uint64_t per_wave = (uint64_t)sms * max_hb;
   const uint64_t waves = n ? (n + per_wave - 1) / per_wave : 0;
   const uint64_t HB = n ? (n + (uint64_t)sms * waves - 1) / ((uint64_t)sms * waves) : 1;
   const uint64_t NB = (n + HB - 1) / HB;
@@ -977,6 +1000,9 @@ int vbdr_plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n, vbdr_plan_t *
   *out = p;
   return VBDR_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int vbdr_plan_destroy(vbdr_plan_t p) {
   if (!p) return VBDR_OK;
@@ -1028,6 +1054,36 @@ int vbdr_estimate_planned(vbdr_t h, vbdr_plan_t p, float *d_out, void *stream) {
   if (!d_out || ((uintptr_t)d_out & 3u)) return VBDR_EINVAL;
   return fail_cuda(h, vbk::launch_planned_estimate(h->d, h->s, h->est, p->dev, d_out,
                                                    (cudaStream_t)stream));
+}
+
+int vbdr_estimate_learned_planned(vbdr_t h, vbdr_mlp_t m, vbdr_plan_t p, float *d_out,
+                                  void *stream) {
+  NvtxRange nvtx("vbdr_estimate_learned_planned");
+  if (!h || !p || !m) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!plan_matches(h, p) || p->dev.HB > vbk::kLearnMaxHB) return VBDR_EINVAL;
+  if (!h->slid) return VBDR_EORDER;
+  const uint64_t n = p->dev.n;
+  if (n == 0) return VBDR_OK;
+  if (!d_out || ((uintptr_t)d_out & 3u)) return VBDR_EINVAL;
+  if (max_log2_g(h->d) > kMaxFeatureLog2G) return VBDR_ERANGE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n > h->feat_cap) {  // the feature rows' buffer, grown outside any capture
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    cudaFree(h->d_feat);
+    h->d_feat = nullptr;
+    h->feat_cap = 0;
+    if (cudaMalloc(&h->d_feat, n * vbk::kMlpLive * sizeof(uint16_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return VBDR_ENOMEM;
+    }
+    h->feat_cap = n;
+  }
+  __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(h->d_feat);
+  cudaError_t e = vbk::launch_planned_features(h->d, h->s, h->est, p->dev, d_out, X, st);
+  if (e == cudaSuccess) e = vbk::launch_mlp_correct(m, X, n, d_out, st);
+  return fail_cuda(h, e);
 }
 
 int vbdr_estimate_planned_host(vbdr_t h, vbdr_plan_t p, float *h_out, void *stream) {

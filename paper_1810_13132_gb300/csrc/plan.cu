@@ -325,7 +325,189 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   }
 }
 
+// ----- the learned correction's features from a plan -----
+// A plan built for the learned correction has at most kLearnMaxHB hosts per
+// block (two waves of one CTA per SM for 1M hosts), so that every host of a
+// block can keep a 32-bin histogram of its register values in shared memory:
+// 32 one-byte bins per host, one shared atomic per plan entry.  A byte bin
+// can only reach 256 when all of a host's g >= 256 registers hold one value;
+// the bins then no longer sum to g, and that host is recounted exactly from
+// the registers (Alg. 3 again, rare).  From the exact counts the block
+// derives what the gather kernel computes -- S, V, the plain estimate, the
+// feature row -- with the same operations, so both paths give the same bits.
+constexpr int kLearnSlots = 2;
+struct LearnSmem {
+  unsigned char ring[kLearnSlots][kChunkBytes];
+  uint4 ents[kLearnSlots][kEntCap / 4];
+  uint32_t bins[kLearnMaxHB + 1][8];  // + the spare slot of padding entries
+  uint64_t full[kLearnSlots], empty[kLearnSlots];
+  double nZZ;
+  int bad;
+};
+static_assert(sizeof(LearnSmem) <= 227 * 1024, "shared memory of one CTA");
+
+__device__ __forceinline__ void take_bin(const unsigned char *ring, uint32_t *bins, uint32_t e,
+                                         unsigned int *chk) {
+  const uint32_t M = ring[e & (kChunkBytes - 1)];
+  if (!vbk_check(M < 32u, chk, kChkPlan)) return;
+  const uint32_t lh = min(e >> kPlanChunkLog2, kLearnMaxHB);
+  atomicAdd(bins + lh * 8 + (M >> 2), 1u << (8u * (M & 3u)));
+}
+
+// Exact histogram of one host's g virtual registers (Alg. 3, gathered).
+__device__ __noinline__ void recount_host(const Dims &d, const DevState &s, uint32_t aip,
+                                          uint32_t g, uint16_t *rc) {
+  for (int m = 0; m < 32; ++m) rc[m] = 0;
+  for (uint32_t i = 0; i < g; ++i) {
+    const uint32_t pidx = reduce32(hash32(aip, s.ktab[i]), d.zmul);
+    if (!vbk_check(pidx < d.Z, s.check, kChkPidx)) continue;
+    const uint32_t M = s.reg[pidx];
+    if (vbk_check(M < 32u, s.check, kChkReg)) rc[M & 31u]++;
+  }
+}
+
+__global__ void __launch_bounds__(kPlanThreads, 1)
+    planned_features_kernel(Dims d, DevState s, EstConst c, PlanDev p, float *__restrict__ out,
+                            __nv_bfloat16 *__restrict__ feat) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  LearnSmem &S = *reinterpret_cast<LearnSmem *>(smem_raw);
+  const uint32_t blk = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t nh = block_hosts(p, blk);
+  for (uint32_t i = threadIdx.x; i < (kLearnMaxHB + 1) * 8; i += blockDim.x) (&S.bins[0][0])[i] = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kLearnSlots; ++i) {
+      mbar_init(&S.full[i], 1);
+      mbar_init(&S.empty[i], kConsumerWarps);
+    }
+    S.nZZ = pool_noise(d, s, c);
+    S.bad = 0;
+  }
+  __syncthreads();
+  const uint32_t nch = p.nchunks;
+  const unsigned long long *goff = p.goff + (uint64_t)blk * nch;
+  if (warp == kConsumerWarps) {
+    if (lane == 0) {
+      bool ok = true;
+      uint32_t issued = 0;
+      for (uint32_t ch = 0; ch < nch; ++ch) {
+        const uint32_t slot = ch % kLearnSlots;
+        if (ch >= (uint32_t)kLearnSlots &&
+            !mbar_wait(&S.empty[slot], (ch / kLearnSlots - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        const unsigned long long ne = goff[ch + 1] - goff[ch];
+        const uint32_t ebytes = 4u * (uint32_t)(ne < kEntCap ? ne : kEntCap);
+        mbar_expect_tx(&S.full[slot], kChunkBytes + ebytes);
+        bulk_load_g2s(S.ring[slot], s.reg + (uint64_t)ch * kChunkBytes, kChunkBytes, &S.full[slot]);
+        if (ebytes) bulk_load_g2s(S.ents[slot], p.entries + goff[ch], ebytes, &S.full[slot]);
+        issued = ch + 1;
+      }
+      const uint32_t first = issued > (uint32_t)kLearnSlots ? issued - kLearnSlots : 0u;
+      for (uint32_t ch = first; ch < issued; ++ch)
+        if (!mbar_wait(&S.full[ch % kLearnSlots], (ch / kLearnSlots) & 1u)) ok = false;
+      if (!ok) S.bad = 1;
+    }
+  } else {
+    const uint32_t t = threadIdx.x, T = kConsumerWarps * 32;
+    uint32_t *bins = &S.bins[0][0];
+    for (uint32_t ch = 0; ch < nch; ++ch) {
+      const uint32_t slot = ch % kLearnSlots;
+      if (!mbar_wait(&S.full[slot], (ch / kLearnSlots) & 1u)) {
+        S.bad = 1;
+        break;
+      }
+      const unsigned char *ring = S.ring[slot];
+      const uint64_t q0 = goff[ch] / 4, nq = goff[ch + 1] / 4 - q0;
+      const uint32_t nq_s = nq < kEntCap / 4 ? (uint32_t)nq : kEntCap / 4;
+      const uint32_t lead = (t + 160u * ch) % T;
+      for (uint32_t q = lead; q < nq_s; q += T) {
+        const uint4 e = S.ents[slot][q];
+        take_bin(ring, bins, e.x, s.check);
+        take_bin(ring, bins, e.y, s.check);
+        take_bin(ring, bins, e.z, s.check);
+        take_bin(ring, bins, e.w, s.check);
+      }
+      const uint4 *grp = reinterpret_cast<const uint4 *>(p.entries) + q0;
+      for (uint64_t q = nq_s + lead; q < nq; q += T) {
+        const uint4 e = ld_stream(grp + q);
+        take_bin(ring, bins, e.x, s.check);
+        take_bin(ring, bins, e.y, s.check);
+        take_bin(ring, bins, e.z, s.check);
+        take_bin(ring, bins, e.w, s.check);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.empty[slot]);
+    }
+  }
+  __syncthreads();
+  const bool bad = S.bad != 0;
+  if (bad && threadIdx.x == 0) atomicOr(p.err, 1u);
+  const double nZZ = S.nZZ;
+  const uint64_t h0 = (uint64_t)blk * p.HB;
+  for (uint32_t lh = threadIdx.x; lh < nh; lh += blockDim.x) {
+    const uint32_t aip = p.aips[h0 + lh];
+    const uint32_t b = host_b(d, aip), g = 1u << b;
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const uint32_t v = S.bins[lh][w];
+      total += (v & 0xffu) + ((v >> 8) & 0xffu) + ((v >> 16) & 0xffu) + (v >> 24);
+    }
+    // a bin overflowed (the bins no longer sum to g): recount this host from
+    // the registers into 16-bit counts
+    const bool slow = total != g;
+    uint16_t rc[32];
+    if (slow) recount_host(d, s, aip, g, rc);
+    auto count = [&](int m) -> uint32_t {
+      return slow ? (uint32_t)rc[m] : (S.bins[lh][m >> 2] >> (8 * (m & 3))) & 0xffu;
+    };
+    unsigned long long Sum = 0;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) Sum += (unsigned long long)count(m) << (32 - m);
+    const uint32_t V = count(0);
+    double n_g = 0.0;
+    const double est = host_estimate(Sum, V, b, c, s.lnv, nZZ, &n_g);
+    const uint64_t row = h0 + lh;
+    out[row] = bad ? __int_as_float(0x7fc00000) : (float)est;
+    // the feature row: bins / g, then the noise statistics (as the gather
+    // kernel writes them), 16 bytes at a time
+    const float inv_g = 1.0f / (float)g;
+    uint4 *dst = reinterpret_cast<uint4 *>(feat + row * kMlpLive);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __align__(16) __nv_bfloat16 x[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = __float2bfloat16((float)count(8 * q + k) * inv_g);
+      dst[q] = *reinterpret_cast<const uint4 *>(x);
+    }
+    __align__(16) __nv_bfloat16 x[16];
+    x[0] = __float2bfloat16((float)b * 0.0625f);
+    x[1] = __float2bfloat16(log1pf((float)est) * 0.0625f);
+    x[2] = __float2bfloat16(log1pf((float)n_g) * 0.0625f);
+    x[3] = __float2bfloat16(log1pf((float)nZZ));
+    x[4] = __float2bfloat16((float)((double)s.sums[1] / (double)d.Z));
+    x[5] = __float2bfloat16((float)V / (float)g);
+#pragma unroll
+    for (int q = 6; q < 16; ++q) x[q] = __float2bfloat16(0.f);
+    dst[4] = reinterpret_cast<const uint4 *>(x)[0];
+    dst[5] = reinterpret_cast<const uint4 *>(x)[1];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_planned_features(const Dims &d, const DevState &s, const EstConst &c,
+                                    const PlanDev &p, float *out, __nv_bfloat16 *feat,
+                                    cudaStream_t st) {
+  if (p.NB == 0) return cudaSuccess;
+  const int smem = (int)sizeof(LearnSmem);
+  cudaError_t e = cudaFuncSetAttribute(planned_features_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  planned_features_kernel<<<p.NB, kPlanThreads, smem, st>>>(d, s, c, p, out, feat);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_plan_count(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st) {
   if (p.NB == 0) return cudaSuccess;

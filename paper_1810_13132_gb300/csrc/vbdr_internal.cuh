@@ -273,6 +273,7 @@ cudaError_t launch_merge_slice_state(const Dims &d, const DevState &s, int layou
 constexpr int kPlanChunkLog2 = 15;
 constexpr uint64_t kPlanChunk = 1ull << kPlanChunkLog2;
 constexpr uint32_t kPlanMaxHB = 7000;       // hosts per block (shared accumulators)
+constexpr uint32_t kLearnMaxHB = 3300;      // hosts per block of a learned-correction plan
 constexpr uint32_t kPlanMaxChunks = 8192;   // Z <= 2^28
 constexpr uint32_t kPlanPad = kPlanMaxHB << kPlanChunkLog2;  // padding: spare host slot
 // Device view of a plan: hosts [blk HB, (blk + 1) HB) form block blk; the
@@ -294,5 +295,8 @@ cudaError_t launch_plan_fill(const Dims &d, const DevState &s, const PlanDev &p,
 cudaError_t launch_plan_sort(const PlanDev &p, cudaStream_t st);
 cudaError_t launch_planned_estimate(const Dims &d, const DevState &s, const EstConst &c,
                                    const PlanDev &p, float *out, cudaStream_t st);
+cudaError_t launch_planned_features(const Dims &d, const DevState &s, const EstConst &c,
+                                    const PlanDev &p, float *out, __nv_bfloat16 *feat,
+                                    cudaStream_t st);
 
 }  // namespace vbk

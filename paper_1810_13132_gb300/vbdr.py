@@ -53,6 +53,8 @@ _SIGS = {
     "vbdr_check_flags": (ctypes.c_int, [_VP, ctypes.POINTER(_U32), ctypes.POINTER(ctypes.c_int)]),
     "vbdr_plan_create": (ctypes.c_int, [_VP, _VP, _U64, ctypes.POINTER(_VP), _VP]),
     "vbdr_plan_destroy": (ctypes.c_int, [_VP]),
+    "vbdr_plan_create_learned": (ctypes.c_int, [_VP, _VP, _U64, ctypes.POINTER(_VP), _VP]),
+    "vbdr_estimate_learned_planned": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "vbdr_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64),
                                       ctypes.POINTER(_U64)]),
     "vbdr_plan_status": (ctypes.c_int, [_VP]),
@@ -266,14 +268,28 @@ class Vbdr:
             self._h, pa, n, po, _stream_ptr(stream)))
 
     # -- planned estimation ----------------------------------------------------
-    def plan(self, aips, stream=None) -> "Plan":
-        """Estimate plan of a host list (int32/uint32 CUDA tensor); see Plan."""
+    def plan(self, aips, stream=None, learned: bool = False) -> "Plan":
+        """Estimate plan of a host list (int32/uint32 CUDA tensor); see Plan.
+        learned=True builds the smaller-block plan the planned learned
+        correction needs (it also serves estimate_planned)."""
         assert aips.is_cuda and aips.is_contiguous()
         n = aips.numel()
         p = ctypes.c_void_p()
-        _check("vbdr_plan_create", self._L.vbdr_plan_create(
+        fn = "vbdr_plan_create_learned" if learned else "vbdr_plan_create"
+        _check(fn, getattr(self._L, fn)(
             self._h, aips.data_ptr() if n else None, n, ctypes.byref(p), _stream_ptr(stream)))
         return Plan(self._L, p, n)
+
+    def estimate_learned_planned(self, mlp: "Mlp", plan: "Plan", out=None, stream=None):
+        """Corrected estimates of a learned plan's hosts (float32 CUDA tensor)."""
+        import torch
+        if out is None:
+            out = torch.empty(plan.n_hosts, dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.numel() >= plan.n_hosts
+        _check("vbdr_estimate_learned_planned", self._L.vbdr_estimate_learned_planned(
+            self._h, mlp._h, plan._p, out.data_ptr() if plan.n_hosts else None,
+            _stream_ptr(stream)))
+        return out
 
     def estimate_planned(self, plan: "Plan", out=None, stream=None):
         """Estimates of the plan's hosts (float32 CUDA tensor, plan order)."""

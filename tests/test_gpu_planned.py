@@ -226,3 +226,70 @@ def test_batched_mixed_g_full_size():
     o.load_virtual_registers(br.aips, br.offsets, br.vregs)
     sample = np.random.default_rng(9).choice(len(br.aips), 20000, replace=False)
     _check_plan(v, plan, br.aips, o, sample)
+
+
+# ------------------------------------------- learned correction through a plan
+
+def _mlp(seed=11):
+    """A network with random parameters (the correction's arithmetic, not its
+    training, is under test) that corrects every host."""
+    from paper_1810_13132_gb300 import Mlp
+    m = Mlp(seed=seed)
+    params, _ = m.get_params()
+    m.set_params(params, 3.0e38)
+    return m
+
+
+def _check_learned(v, aips_np, mlp):
+    """planned learned == gather learned, bit for bit (features, plain
+    estimates and the network are the same arithmetic)."""
+    aips = _dev(aips_np)
+    plan = v.plan(aips, learned=True)
+    got = v.estimate_learned_planned(mlp, plan).cpu().numpy()
+    ref = v.estimate_learned(mlp, aips).cpu().numpy()
+    np.testing.assert_array_equal(got.view(np.uint32), ref.view(np.uint32))
+    # the learned plan also serves the plain planned estimate
+    np.testing.assert_array_equal(v.estimate_planned(plan).cpu().numpy().view(np.uint32),
+                                  v.estimate(aips).cpu().numpy().view(np.uint32))
+    plan.status()
+    plan.close()
+
+
+def test_learned_planned_equals_gather_trace_shape():
+    """Trace-shaped traffic at 1/16 (4M pairs per slice, 62500 hosts, g = 256,
+    Z = 2^20), several slices; the host list takes several blocks and a
+    ragged last block."""
+    gen = traffic.ZipfTraffic(62_500, 1.05, 2_000_000 // 16, 30, seed=230, repeat_frac=0.10)
+    v, _ = _make("gfast", 30, 1 << 20, 8)
+    for _ in range(4):
+        v.scan(_dev(gen.next_slice(1 << 22)))
+        v.slide()
+    _check_learned(v, gen.aips, _mlp())
+
+
+def test_learned_planned_overflowing_bins_and_mixed_g():
+    """An empty pool: every register is 0, so every host's histogram has a
+    single bin of g >= 256 counts -- more than a byte bin holds -- and the
+    exact recount must take over; then the same hosts (g = 64..512) after
+    traffic."""
+    rng = np.random.default_rng(231)
+    aips = traffic.distinct_u32(rng, 9000)
+    v, _ = _make("gsmall", 6, (1 << 18) + 77, 9, b_min=6, group_rule=1)
+    v.slide()  # one empty slice: all registers 0
+    _check_learned(v, aips, _mlp(12))
+    for _ in range(3):
+        v.scan(_dev(traffic.uniform_pairs(rng, 300_000, aips)))
+        v.slide()
+    _check_learned(v, aips, _mlp(13))
+
+
+def test_learned_planned_refuses_a_plain_plan():
+    from paper_1810_13132_gb300 import VbdrError
+    rng = np.random.default_rng(232)
+    aips = traffic.distinct_u32(rng, 600_000)  # more than 3300 hosts per block of a wave
+    v, _ = _make("gfast", 3, 1 << 16, 7)
+    v.slide()
+    plan = v.plan(_dev(aips))  # blocks of up to 7000 hosts: here about 3950
+    with pytest.raises(VbdrError) as e:
+        v.estimate_learned_planned(_mlp(), plan)
+    assert e.value.code == -1
