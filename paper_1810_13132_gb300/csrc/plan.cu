@@ -335,10 +335,14 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
 // the registers (Alg. 3 again, rare).  From the exact counts the block
 // derives what the gather kernel computes -- S, V, the plain estimate, the
 // feature row -- with the same operations, so both paths give the same bits.
-constexpr int kLearnSlots = 2;
+constexpr int kLearnSlots = 3;
+// a learned plan's groups average HB g / chunks (1650 entries for 1M hosts of
+// g = 256 over 2^24 registers); the first kLearnEntCap are staged, any rest is
+// read from global memory
+constexpr uint32_t kLearnEntCap = 2048;
 struct LearnSmem {
   unsigned char ring[kLearnSlots][kChunkBytes];
-  uint4 ents[kLearnSlots][kEntCap / 4];
+  uint4 ents[kLearnSlots][kLearnEntCap / 4];
   uint32_t bins[kLearnMaxHB + 1][8];  // + the spare slot of padding entries
   uint64_t full[kLearnSlots], empty[kLearnSlots];
   double nZZ;
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
           break;
         }
         const unsigned long long ne = goff[ch + 1] - goff[ch];
-        const uint32_t ebytes = 4u * (uint32_t)(ne < kEntCap ? ne : kEntCap);
+        const uint32_t ebytes = 4u * (uint32_t)(ne < kLearnEntCap ? ne : kLearnEntCap);
         mbar_expect_tx(&S.full[slot], kChunkBytes + ebytes);
         bulk_load_g2s(S.ring[slot], s.reg + (uint64_t)ch * kChunkBytes, kChunkBytes, &S.full[slot]);
         if (ebytes) bulk_load_g2s(S.ents[slot], p.entries + goff[ch], ebytes, &S.full[slot]);
@@ -419,7 +423,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       }
       const unsigned char *ring = S.ring[slot];
       const uint64_t q0 = goff[ch] / 4, nq = goff[ch + 1] / 4 - q0;
-      const uint32_t nq_s = nq < kEntCap / 4 ? (uint32_t)nq : kEntCap / 4;
+      const uint32_t nq_s = nq < kLearnEntCap / 4 ? (uint32_t)nq : kLearnEntCap / 4;
       const uint32_t lead = (t + 160u * ch) % T;
       for (uint32_t q = lead; q < nq_s; q += T) {
         const uint4 e = S.ents[slot][q];
