@@ -51,6 +51,9 @@ def _args():
     p.add_argument("--estimate", default="planned", choices=["planned", "gather"],
                    help="trace/small: estimate through a host-list plan (built once, outside "
                         "the timed steps) or by gathering every virtual register")
+    p.add_argument("--scan", default="direct", choices=["direct", "bucketed"],
+                   help="trace/small: the scan kernel of the timed step (bucketed: opt-in "
+                        "owner-computes prototype)")
     p.add_argument("--no-learned", action="store_true", help="serve: plain estimates only")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-mre", action="store_true")
@@ -217,6 +220,7 @@ def run_ours(a):
     d_aips = torch.from_numpy(gen.aips.view(np.int32)).cuda()
     d_out = torch.empty(H, dtype=torch.float32, device="cuda")
     v = Vbdr(Config(k=wl["k"], num_bdr=wl["Z"], log2_g=wl["log2_g"], layout=a.layout, seed=SEED))
+    v.set_scan_mode(a.scan)
     stream = torch.cuda.current_stream()
     planned = a.estimate == "planned"
     plan = plan_info = None
@@ -449,7 +453,7 @@ def run_ours(a):
         "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
-        "config": {"workload": wl["name"] + f" {a.layout}", "layout": a.layout,
+        "config": {"workload": wl["name"] + f" {a.layout}", "layout": a.layout, "scan": a.scan,
                    "k": wl["k"], "pairs_per_slice": N, "hosts": H, "Z": Z,
                    "g": 1 << wl["log2_g"], "repeat_frac": wl["repeat_frac"],
                    "l2": "inputs larger than L2 (512 MiB per slice, 4 distinct slices cycled)",

@@ -329,7 +329,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
 // A plan built for the learned correction has at most kLearnMaxHB hosts per
 // block (two waves of one CTA per SM for 1M hosts), so that every host of a
 // block can keep a 32-bin histogram of its register values in shared memory:
-// 32 one-byte bins per host, one shared atomic per plan entry.  A byte bin
+// 32 one-byte bins per host (8 words, the word of value M at (M / 4) xor
+// (host mod 8)), one shared atomic per plan entry.  A byte bin
 // can only reach 256 when all of a host's g >= 256 registers hold one value;
 // the bins then no longer sum to g, and that host is recounted exactly from
 // the registers (Alg. 3 again, rare).  From the exact counts the block
@@ -355,7 +356,10 @@ __device__ __forceinline__ void take_bin(const unsigned char *ring, uint32_t *bi
   const uint32_t M = ring[e & (kChunkBytes - 1)];
   if (!vbk_check(M < 32u, chk, kChkPlan)) return;
   const uint32_t lh = min(e >> kPlanChunkLog2, kLearnMaxHB);
-  atomicAdd(bins + lh * 8 + (M >> 2), 1u << (8u * (M & 3u)));
+  // word (M / 4) of the host's 8, swizzled by the host index: the values of
+  // one warp's entries cluster, so without it their atomics fall in the few
+  // banks 8 lh + const
+  atomicAdd(bins + lh * 8 + ((M >> 2) ^ (lh & 7u)), 1u << (8u * (M & 3u)));
 }
 
 // Exact histogram of one host's g virtual registers (Alg. 3, gathered).
@@ -464,7 +468,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     uint16_t rc[32];
     if (slow) recount_host(d, s, aip, g, rc);
     auto count = [&](int m) -> uint32_t {
-      return slow ? (uint32_t)rc[m] : (S.bins[lh][m >> 2] >> (8 * (m & 3))) & 0xffu;
+      return slow ? (uint32_t)rc[m]
+                  : (S.bins[lh][(uint32_t)(m >> 2) ^ (lh & 7u)] >> (8 * (m & 3))) & 0xffu;
     };
     unsigned long long Sum = 0;
 #pragma unroll
