@@ -524,6 +524,11 @@ def run_extras(a, wl, slices, d_slices, plan, d_aips, peak):
         out["serve"] = serve_core(a, tenants=2, slices_per_tenant=40, warmup=3)
     except Exception as e:
         out["serve"] = {"error": repr(e)}
+    try:  # the same service with one slice in flight per tenant: no queueing
+        out["serve_one_in_flight"] = serve_core(a, tenants=2, slices_per_tenant=40, warmup=3,
+                                                inflight=1)
+    except Exception as e:
+        out["serve_one_in_flight"] = {"error": repr(e)}
     return out
 
 
@@ -680,12 +685,14 @@ def run_batched(a):
 
 # ------------------------------------------------------ streaming service arm
 
-def serve_core(a, tenants, slices_per_tenant, warmup):
+def serve_core(a, tenants, slices_per_tenant, warmup, inflight=2):
     """Streaming service: slices of log-uniform size in [1M, 128M] pairs
     (8M active hosts, Zipf 1.1 host weights, bursty superspreaders at 0.01%),
     k = 30, Z = 2^26, g = 256; every slice is one CUDA graph replay of scan +
     slide + estimate of all 8M hosts + learned correction + copy-back, with
-    several tenants served at once."""
+    several tenants served at once.  inflight: slices a tenant keeps
+    submitted (2: the next slice's copy overlaps the current graph; 1: each
+    slice waits for the previous one's result before it is submitted)."""
     import threading
     import torch
     from paper_1810_13132_gb300 import Config, Mlp, Server
@@ -724,7 +731,7 @@ def serve_core(a, tenants, slices_per_tenant, warmup):
 
             def run(j, timed):
                 pending.append((srv.submit(t, pool[offs[j]:offs[j] + int(sizes[j])]), j, timed))
-                if len(pending) == 2:
+                if len(pending) == inflight:
                     tk, jj, tt = pending.pop(0)
                     dms, ems = srv.wait(t, tk, out)
                     if tt:
@@ -771,7 +778,7 @@ def serve_core(a, tenants, slices_per_tenant, warmup):
     e2e = np.array(lat["e2e"])
     return {
         "workload": wl["name"], "tenants": tenants, "hosts_per_tenant": wl["n_hosts"],
-        "learned_correction": mlp is not None,
+        "learned_correction": mlp is not None, "slices_in_flight_per_tenant": inflight,
         "value": round(pairs_done[0] / wall / 1e9, 3), "unit": "G pairs/s",
         "slices": int(len(dev)), "warmup_slices": warmup * tenants,
         "latency_ms": {"device_p50": float(np.percentile(dev, 50)),
