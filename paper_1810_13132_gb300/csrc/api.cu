@@ -991,7 +991,7 @@ int plan_create(vbdr_t h, const uint32_t *d_aips, uint64_t n, uint32_t max_hb, v
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(pd.goff, goff.data(), (ngroups + 1) * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = vbk::launch_plan_fill(d, h->s, pd, st);
-  if (e == cudaSuccess) e = vbk::launch_plan_sort(pd, st);
+  if (e == cudaSuccess) e = vbk::launch_plan_sort(pd, max_hb <= vbk::kLearnMaxHB, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(e);
   cudaFree(pd.counts);

@@ -121,15 +121,22 @@ __global__ void __launch_bounds__(kBuildThreads)
 // Building, pass 3: the order of a group's staged entries (the first
 // kEntCap) is chosen so that the 32 entries one warp instruction takes --
 // lane L holds the uint4 at position 32 r + L, so for component j the
-// entries at 128 r + 4 L + j -- read the register chunk in 32 different
-// shared-memory banks wherever the group allows it: entry positions with
-// (pos >> 2) mod 32 = b are given to entries whose register byte lies in
-// bank b, in order; the entries left over fill the remaining positions.
-// The sums are order independent, so the estimates do not change.
+// entries at 128 r + 4 L + j -- meet 32 different shared-memory banks
+// wherever the group allows it: entry positions with (pos >> 2) mod 32 = b
+// are given to entries of bank b, in order; the entries left over fill the
+// remaining positions.  The bank is the register byte's (plain plans: the
+// chunk reads) or the host's (learned plans: the histogram atomics, see
+// take_bin).  The sums are order independent, so the results do not change.
 constexpr uint32_t kSortThreads = 1024;
+// The bank an entry's position asks for: its register byte's bank (plain
+// plans: the reads of the chunk then take distinct banks), or its host's
+// index mod 32 (learned plans: the histogram atomics' bank follows the host)
+__device__ __forceinline__ uint32_t sort_bank(uint32_t e, int by_host) {
+  return by_host ? (e >> kPlanChunkLog2) & 31u : ((e & (kChunkBytes - 1)) >> 2) & 31u;
+}
 constexpr size_t kSortSmem = kEntCap * (3 * sizeof(uint32_t) + sizeof(uint16_t));
 __global__ void __launch_bounds__(kSortThreads)
-    plan_sort_kernel(PlanDev p) {
+    plan_sort_kernel(PlanDev p, int by_host) {
   extern __shared__ uint32_t sort_smem[];  // kSortSmem bytes
   uint32_t *in = sort_smem, *out = sort_smem + kEntCap, *hole = sort_smem + 2 * kEntCap;
   uint16_t *rank = reinterpret_cast<uint16_t *>(sort_smem + 3 * kEntCap);
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(kSortThreads)
     for (uint32_t i = tid; i < P; i += kSortThreads) {
       const uint32_t e = p.entries[q0 + i];
       in[i] = e;
-      rank[i] = (uint16_t)atomicAdd(&cnt[((e & (kChunkBytes - 1)) >> 2) & 31u], 1u);
+      rank[i] = (uint16_t)atomicAdd(&cnt[sort_bank(e, by_host)], 1u);
     }
     // positions of bank b: 128 r + 4 b + j < P
     if (tid < 32) {
@@ -158,7 +165,7 @@ __global__ void __launch_bounds__(kSortThreads)
     for (uint32_t i = tid; i < P; i += kSortThreads) out[i] = 0xffffffffu;
     __syncthreads();
     for (uint32_t i = tid; i < P; i += kSortThreads) {
-      const uint32_t e = in[i], b = ((e & (kChunkBytes - 1)) >> 2) & 31u, k = rank[i];
+      const uint32_t e = in[i], b = sort_bank(e, by_host), k = rank[i];
       if (k < cap[b]) out[128 * (k >> 2) + 4 * b + (k & 3)] = e;
     }
     __syncthreads();
@@ -194,7 +201,7 @@ __global__ void __launch_bounds__(kSortThreads)
     }
     __syncthreads();
     for (uint32_t i = tid; i < P; i += kSortThreads) {
-      const uint32_t e = in[i], b = ((e & (kChunkBytes - 1)) >> 2) & 31u;
+      const uint32_t e = in[i], b = sort_bank(e, by_host);
       if (rank[i] >= cap[b]) out[hole[atomicAdd(&n_left, 1u)]] = e;
     }
     __syncthreads();
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
 // block (two waves of one CTA per SM for 1M hosts), so that every host of a
 // block can keep a 32-bin histogram of its register values in shared memory:
 // 32 one-byte bins per host (8 words, the word of value M at (M / 4) xor
-// (host mod 8)), one shared atomic per plan entry.  A byte bin
+// (host / 4 mod 8)), one shared atomic per plan entry.  A byte bin
 // can only reach 256 when all of a host's g >= 256 registers hold one value;
 // the bins then no longer sum to g, and that host is recounted exactly from
 // the registers (Alg. 3 again, rare).  From the exact counts the block
@@ -356,10 +363,11 @@ __device__ __forceinline__ void take_bin(const unsigned char *ring, uint32_t *bi
   const uint32_t M = ring[e & (kChunkBytes - 1)];
   if (!vbk_check(M < 32u, chk, kChkPlan)) return;
   const uint32_t lh = min(e >> kPlanChunkLog2, kLearnMaxHB);
-  // word (M / 4) of the host's 8, swizzled by the host index: the values of
-  // one warp's entries cluster, so without it their atomics fall in the few
-  // banks 8 lh + const
-  atomicAdd(bins + lh * 8 + ((M >> 2) ^ (lh & 7u)), 1u << (8u * (M & 3u)));
+  // word (M / 4) of the host's 8, swizzled by host bits 2..4: the values of
+  // one warp's entries cluster, so without it their atomics fall in the
+  // banks 8 lh + const; with it the bank is 8 (lh mod 4) + (M / 4 xor
+  // (lh / 4 mod 8)), all 32 banks for 32 consecutive hosts
+  atomicAdd(bins + lh * 8 + ((M >> 2) ^ ((lh >> 2) & 7u)), 1u << (8u * (M & 3u)));
 }
 
 // Exact histogram of one host's g virtual registers (Alg. 3, gathered).
@@ -469,7 +477,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     if (slow) recount_host(d, s, aip, g, rc);
     auto count = [&](int m) -> uint32_t {
       return slow ? (uint32_t)rc[m]
-                  : (S.bins[lh][(uint32_t)(m >> 2) ^ (lh & 7u)] >> (8 * (m & 3))) & 0xffu;
+                  : (S.bins[lh][(uint32_t)(m >> 2) ^ ((lh >> 2) & 7u)] >> (8 * (m & 3))) & 0xffu;
     };
     unsigned long long Sum = 0;
 #pragma unroll
@@ -530,12 +538,12 @@ cudaError_t launch_plan_fill(const Dims &d, const DevState &s, const PlanDev &p,
   return cudaGetLastError();
 }
 
-cudaError_t launch_plan_sort(const PlanDev &p, cudaStream_t st) {
+cudaError_t launch_plan_sort(const PlanDev &p, bool by_host, cudaStream_t st) {
   if (p.NB == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(plan_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kSortSmem);
   if (e != cudaSuccess) return e;
-  plan_sort_kernel<<<p.NB, kSortThreads, kSortSmem, st>>>(p);
+  plan_sort_kernel<<<p.NB, kSortThreads, kSortSmem, st>>>(p, by_host ? 1 : 0);
   return cudaGetLastError();
 }
 

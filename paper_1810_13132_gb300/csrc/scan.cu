@@ -13,7 +13,7 @@
 // state after the scan does not depend on thread order, and an update whose
 // effect is already visible can be dropped.
 //
-// Design (measured on GB300, see the design notes):
+// Design (each choice measured on GB300):
 //   * streaming: 16-byte loads of two pairs (L1::no_allocate), UNROLL loads
 //     in flight per thread, grid-stride over the slice;
 //   * hashing: the 64-bit mix evaluated in 32-bit halves with the seed terms
@@ -28,6 +28,11 @@
 //     word are merged first.  A warp-wide match.any de-duplication was
 //     measured 3x slower than no de-duplication at all on this part (it runs
 //     on the ADU pipe), so it is not used.
+// The one random test load per pair is the limit: the L1TEX pipe serves
+// about one such request per SM clock, 64M tests need about 0.2 ms, and the
+// kernel takes 0.30 ms on a 64M-pair slice whatever the loads in flight per
+// thread (2 to 8) or the register budget.  bucket.cu routes the updates to
+// shared memory instead; it is exact too but slower on this part.
 #include "vbdr_internal.cuh"
 
 namespace vbk {

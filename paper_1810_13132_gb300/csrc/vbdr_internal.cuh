@@ -292,7 +292,7 @@ struct PlanDev {
 };
 cudaError_t launch_plan_count(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st);
 cudaError_t launch_plan_fill(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st);
-cudaError_t launch_plan_sort(const PlanDev &p, cudaStream_t st);
+cudaError_t launch_plan_sort(const PlanDev &p, bool by_host, cudaStream_t st);
 cudaError_t launch_planned_estimate(const Dims &d, const DevState &s, const EstConst &c,
                                    const PlanDev &p, float *out, cudaStream_t st);
 cudaError_t launch_planned_features(const Dims &d, const DevState &s, const EstConst &c,
