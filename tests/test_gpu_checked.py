@@ -1,8 +1,9 @@
 """The bounds-checked build (libvbdr_check.so, -DVBDR_CHECK) on the GPU:
 every kernel tests its physical indices, LBP1 and register values and
 records a violation instead of making the access.  A run through every
-layout, the planned estimate, LogLog / PCSA, batched registers and the
-learned correction must match the oracle and leave no violation recorded.
+layout, the planned estimate, LogLog / PCSA, batched registers, the learned
+correction (gathered and planned), the bucketed scan and the multi-rank
+calls must match the oracle and leave no violation recorded.
 
 Runs in a child process, because a process loads one of the two builds."""
 import os
@@ -66,6 +67,36 @@ o.load_virtual_registers(br.aips, br.offsets, br.vregs)
 close(v.estimate(torch.from_numpy(br.aips.view(np.int32)).cuda()).cpu().numpy(), o.estimate(br.aips))
 flags, checked = v.check_flags()
 assert checked and flags == 0, flags
+
+# the opt-in bucketed scan, the learned plan and the multi-rank calls
+gen = traffic.ZipfTraffic(5000, 1.05, 60_000, 5, seed=903, repeat_frac=0.1)
+d_aips = torch.from_numpy(gen.aips.view(np.int32)).cuda()
+for layout in ("gfast", "gsmall"):
+    v = Vbdr(Config(k=5, num_bdr=(1 << 18) + 77, log2_g=8, layout=layout, seed=SEED))
+    v.set_scan_mode("bucketed")
+    o = oracle.Oracle(layout, k=5, Z=(1 << 18) + 77, b=8, seed=SEED)
+    w = Vbdr(Config(k=5, num_bdr=(1 << 18) + 77, log2_g=8, layout=layout, seed=SEED))
+    for t in range(3):
+        s = gen.next_slice(600_001)
+        d_s = torch.from_numpy(s.view(np.int32)).cuda()
+        v.scan(d_s)
+        o.scan(s)
+        recs, fill = w.route_records(d_s, 2)
+        f = fill.cpu()
+        w.apply_records(torch.cat([recs[r, :int(f[r])] for r in range(2)]))
+        v.slide(); o.slide(); w.slide()
+        np.testing.assert_array_equal(v.registers(), o.state()["reg"])
+        np.testing.assert_array_equal(w.registers(), o.state()["reg"])
+    lplan = v.plan(d_aips, learned=True)
+    m = Mlp(seed=4)
+    np.testing.assert_array_equal(v.estimate_learned_planned(m, lplan).cpu().numpy(),
+                                  v.estimate_learned(m, d_aips).cpu().numpy())
+    w.merge_slice_state(v.slice_state())
+    w.set_registers(v.registers_device(), v.pcsa_device() if layout == "gsmall" else None)
+    close(w.estimate(d_aips).cpu().numpy(), o.estimate(gen.aips))
+    for h in (v, w):
+        flags, checked = h.check_flags()
+        assert checked and flags == 0, (layout, flags)
 print("checked build: no violation")
 '''
 
