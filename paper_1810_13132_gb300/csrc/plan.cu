@@ -284,14 +284,18 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   } else {
     const uint32_t t = threadIdx.x, T = kConsumerWarps * 32;
     uint32_t *acc = &S.acc[0][0];
+    // the group offsets are read one chunk ahead: a load at the top of each
+    // chunk would put an L2 round trip on every iteration's critical path
+    unsigned long long g_lo = goff[0], g_hi = goff[1];
     for (uint32_t ch = 0; ch < nch; ++ch) {
+      const unsigned long long g_next = ch + 2 <= nch ? goff[ch + 2] : g_hi;
       const uint32_t slot = ch % kPlanSlots;
       if (!mbar_wait(&S.full[slot], (ch / kPlanSlots) & 1u)) {
         S.bad = 1;
         break;
       }
       const unsigned char *ring = S.ring[slot];
-      const uint64_t q0 = goff[ch] / 4, nq = goff[ch + 1] / 4 - q0;
+      const uint64_t q0 = g_lo / 4, nq = g_hi / 4 - q0;
       const uint32_t nq_s = nq < kEntCap / 4 ? (uint32_t)nq : kEntCap / 4;
       // thread t starts at uint4 (t + 160 ch) mod T: the threads left
       // without work by a group smaller than T move by five warps from
@@ -315,6 +319,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.empty[slot]);
+      g_lo = g_hi;
+      g_hi = g_next;
     }
   }
   __syncthreads();
@@ -427,14 +433,18 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   } else {
     const uint32_t t = threadIdx.x, T = kConsumerWarps * 32;
     uint32_t *bins = &S.bins[0][0];
+    // the group offsets are read one chunk ahead: a load at the top of each
+    // chunk would put an L2 round trip on every iteration's critical path
+    unsigned long long g_lo = goff[0], g_hi = goff[1];
     for (uint32_t ch = 0; ch < nch; ++ch) {
+      const unsigned long long g_next = ch + 2 <= nch ? goff[ch + 2] : g_hi;
       const uint32_t slot = ch % kLearnSlots;
       if (!mbar_wait(&S.full[slot], (ch / kLearnSlots) & 1u)) {
         S.bad = 1;
         break;
       }
       const unsigned char *ring = S.ring[slot];
-      const uint64_t q0 = goff[ch] / 4, nq = goff[ch + 1] / 4 - q0;
+      const uint64_t q0 = g_lo / 4, nq = g_hi / 4 - q0;
       const uint32_t nq_s = nq < kLearnEntCap / 4 ? (uint32_t)nq : kLearnEntCap / 4;
       const uint32_t lead = (t + 160u * ch) % T;
       for (uint32_t q = lead; q < nq_s; q += T) {
@@ -454,6 +464,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.empty[slot]);
+      g_lo = g_hi;
+      g_hi = g_next;
     }
   }
   __syncthreads();
