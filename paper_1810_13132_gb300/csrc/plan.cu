@@ -36,7 +36,6 @@
 namespace vbk {
 namespace {
 
-constexpr int kPlanSlots = 3;
 constexpr uint32_t kEntCap = 4096;  // entries of a group staged in shared memory
 constexpr int kConsumerWarps = 31;
 constexpr int kPlanThreads = (kConsumerWarps + 1) * 32;
@@ -210,17 +209,131 @@ __global__ void __launch_bounds__(kSortThreads)
   }
 }
 
-// Shared memory of the planned estimate.
+// ----- the ring of the planned kernels -----
+// A 3-slot shared-memory ring; slot k holds one step: a 32 KiB register chunk
+// (from L2, the register array is small) and the chunk's group of entries
+// (its first ECAP entries, from DRAM), both TMA bulk copies completing on the
+// slot's full barrier.  Beside them the producer leaves the group's size (in
+// uint4s) and offset, so the consumers need no global load per step.  Block
+// blk visits the chunks in the rotated order c0, c0 + 1, ... (mod nchunks)
+// from c0 = blk nchunks / NB: at any moment the blocks read different
+// chunks, where a common order makes all SMs read one chunk at once and
+// concentrates the register stream on a few L2 slices.
+constexpr uint32_t kRingSlots = 3;
+template <uint32_t ECAP>
+struct PlanRing {
+  unsigned char reg[kRingSlots][kChunkBytes];
+  uint4 ents[kRingSlots][ECAP / 4];
+  unsigned long long lo[kRingSlots];
+  uint32_t nq[kRingSlots];
+  uint64_t full[kRingSlots], empty[kRingSlots];
+};
+
+__device__ __forceinline__ uint32_t first_chunk(uint32_t blk, uint32_t nblk, uint32_t nch) {
+  return (uint32_t)(((uint64_t)blk * nch) / nblk);
+}
+
+template <uint32_t ECAP>
+__device__ void ring_init(PlanRing<ECAP> &r) {
+  for (uint32_t i = 0; i < kRingSlots; ++i) {
+    mbar_init(&r.full[i], 1);
+    mbar_init(&r.empty[i], kConsumerWarps);
+  }
+}
+
+// The producer (one thread): step ch into slot ch mod 3 once the consumers
+// released the slot's previous step.  false if a wait expired; every copy it
+// issued has landed (or its wait expired) when it returns.
+template <uint32_t ECAP>
+__device__ bool ring_produce(PlanRing<ECAP> &r, const DevState &s, const PlanDev &p,
+                             const unsigned long long *goff, uint32_t c0, uint32_t nch) {
+  bool ok = true;
+  uint32_t issued = 0, cc = c0, slot = 0, par = 0;
+  for (uint32_t ch = 0; ch < nch; ++ch) {
+    if (ch >= kRingSlots && !mbar_wait(&r.empty[slot], par ^ 1u)) {
+      ok = false;
+      break;
+    }
+    const unsigned long long lo = goff[cc], ne = goff[cc + 1] - lo;
+    const uint32_t bytes = 4u * (uint32_t)(ne < ECAP ? ne : ECAP);
+    // published to the consumers by the arrive below (release) and their
+    // wait on the barrier (acquire)
+    r.lo[slot] = lo;
+    r.nq[slot] = (uint32_t)(ne >> 2);
+    mbar_expect_tx(&r.full[slot], kChunkBytes + bytes);
+    bulk_load_g2s(r.reg[slot], s.reg + (uint64_t)cc * kChunkBytes, kChunkBytes, &r.full[slot]);
+    if (bytes) bulk_load_g2s(r.ents[slot], p.entries + lo, bytes, &r.full[slot]);
+    issued = ch + 1;
+    if (++cc == nch) cc = 0;
+    if (++slot == kRingSlots) {
+      slot = 0;
+      par ^= 1u;
+    }
+  }
+  // the last phase of every slot used: each issued copy lands before the
+  // block may finish
+  for (uint32_t ch = issued > kRingSlots ? issued - kRingSlots : 0u; ch < issued; ++ch)
+    if (!mbar_wait(&r.full[ch % kRingSlots], (ch / kRingSlots) & 1u)) ok = false;
+  return ok;
+}
+
+// The consumers (warps 0 .. kConsumerWarps - 1): for every step, take(ring,
+// e) on each entry of the step's group (ring: the step's register chunk).
+// Thread t starts at uint4 (t + 160 step) mod T of a group: the threads left
+// without work by a group smaller than T move by five warps from step to
+// step, so no warp idles more than the others.  A group larger than ECAP is
+// finished from global memory.  false if a wait expired.
+template <uint32_t ECAP, class Take>
+__device__ bool ring_consume(PlanRing<ECAP> &r, const PlanDev &p, uint32_t nch, Take &&take) {
+  const uint32_t T = kConsumerWarps * 32, lane = threadIdx.x & 31u;
+  uint32_t lead = threadIdx.x, slot = 0, par = 0;
+  for (uint32_t ch = 0; ch < nch; ++ch) {
+    if (!mbar_wait(&r.full[slot], par)) return false;
+    const unsigned char *ring = r.reg[slot];
+    const uint4 *ents = r.ents[slot];
+    const uint32_t nq = r.nq[slot], nq_s = min(nq, ECAP / 4);
+    for (uint32_t q = lead; q < nq_s; q += T) {
+      const uint4 e = ents[q];
+      take(ring, e.x);
+      take(ring, e.y);
+      take(ring, e.z);
+      take(ring, e.w);
+    }
+    if (nq > ECAP / 4) {
+      const uint4 *grp = reinterpret_cast<const uint4 *>(p.entries) + (r.lo[slot] >> 2);
+      for (uint32_t q = ECAP / 4 + lead; q < nq; q += T) {
+        const uint4 e = ld_stream(grp + q);
+        take(ring, e.x);
+        take(ring, e.y);
+        take(ring, e.z);
+        take(ring, e.w);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&r.empty[slot]);
+    lead += 160u;
+    if (lead >= T) lead -= T;
+    if (++slot == kRingSlots) {
+      slot = 0;
+      par ^= 1u;
+    }
+  }
+  return true;
+}
+
+// ----- the planned estimate -----
+// Per host three 32-bit sums, one shared atomic per plan entry:
+//   M = 0      -> V   += 1                 (contributes 2^32 to S)
+//   M in 1..16 -> Shi += 2^(16 - M)        (2^(32-M) = Shi unit 2^16)
+//   M > 16     -> Slo += 2^(32 - M)
+// so S = V 2^32 + Shi 2^16 + Slo exactly (each field < 2^32 for g <= 2^16).
 constexpr uint32_t kAccRow = kPlanMaxHB + 1;  // + the spare slot of padding entries
 struct PlanSmem {
-  unsigned char ring[kPlanSlots][kChunkBytes];
-  uint4 ents[kPlanSlots][kEntCap / 4];  // the group's first kEntCap entries
+  PlanRing<kEntCap> r;
   uint32_t acc[3][kAccRow];  // V, Shi, Slo
-  uint64_t full[kPlanSlots], empty[kPlanSlots];
   double nZZ;
   int bad;
 };
-
 static_assert(sizeof(PlanSmem) <= 227 * 1024, "shared memory of one CTA");
 
 // One entry: register M of the chunk in the ring, added to its host's sums.
@@ -243,85 +356,23 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   PlanSmem &S = *reinterpret_cast<PlanSmem *>(smem_raw);
   const uint32_t blk = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t nh = block_hosts(p, blk);
-  for (uint32_t i = threadIdx.x; i < kAccRow; i += blockDim.x)
-    S.acc[0][i] = S.acc[1][i] = S.acc[2][i] = 0;
+  for (uint32_t i = threadIdx.x; i < 3 * kAccRow; i += blockDim.x) (&S.acc[0][0])[i] = 0;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kPlanSlots; ++i) {
-      mbar_init(&S.full[i], 1);
-      mbar_init(&S.empty[i], kConsumerWarps);
-    }
+    ring_init(S.r);
     S.nZZ = pool_noise(d, s, c);
     S.bad = 0;
   }
   __syncthreads();
-  const uint32_t nch = p.nchunks;
+  const uint32_t nch = p.nchunks, c0 = first_chunk(blk, p.NB, nch);
   const unsigned long long *goff = p.goff + (uint64_t)blk * nch;
   if (warp == kConsumerWarps) {
-    // producer: chunk c and its entries into slot c % 3 once the consumers
-    // released it
-    if (lane == 0) {
-      bool ok = true;
-      uint32_t issued = 0;
-      for (uint32_t ch = 0; ch < nch; ++ch) {
-        const uint32_t slot = ch % kPlanSlots;
-        if (ch >= (uint32_t)kPlanSlots && !mbar_wait(&S.empty[slot], (ch / kPlanSlots - 1) & 1u)) {
-          ok = false;
-          break;
-        }
-        const unsigned long long ne = goff[ch + 1] - goff[ch];
-        const uint32_t ebytes = 4u * (uint32_t)(ne < kEntCap ? ne : kEntCap);
-        mbar_expect_tx(&S.full[slot], kChunkBytes + ebytes);
-        bulk_load_g2s(S.ring[slot], s.reg + (uint64_t)ch * kChunkBytes, kChunkBytes, &S.full[slot]);
-        if (ebytes) bulk_load_g2s(S.ents[slot], p.entries + goff[ch], ebytes, &S.full[slot]);
-        issued = ch + 1;
-      }
-      // every issued copy lands before the block may finish
-      const uint32_t first = issued > (uint32_t)kPlanSlots ? issued - kPlanSlots : 0u;
-      for (uint32_t ch = first; ch < issued; ++ch)
-        if (!mbar_wait(&S.full[ch % kPlanSlots], (ch / kPlanSlots) & 1u)) ok = false;
-      if (!ok) S.bad = 1;
-    }
+    if (lane == 0 && !ring_produce(S.r, s, p, goff, c0, nch)) S.bad = 1;
   } else {
-    const uint32_t t = threadIdx.x, T = kConsumerWarps * 32;
     uint32_t *acc = &S.acc[0][0];
-    // the group offsets are read one chunk ahead: a load at the top of each
-    // chunk would put an L2 round trip on every iteration's critical path
-    unsigned long long g_lo = goff[0], g_hi = goff[1];
-    for (uint32_t ch = 0; ch < nch; ++ch) {
-      const unsigned long long g_next = ch + 2 <= nch ? goff[ch + 2] : g_hi;
-      const uint32_t slot = ch % kPlanSlots;
-      if (!mbar_wait(&S.full[slot], (ch / kPlanSlots) & 1u)) {
-        S.bad = 1;
-        break;
-      }
-      const unsigned char *ring = S.ring[slot];
-      const uint64_t q0 = g_lo / 4, nq = g_hi / 4 - q0;
-      const uint32_t nq_s = nq < kEntCap / 4 ? (uint32_t)nq : kEntCap / 4;
-      // thread t starts at uint4 (t + 160 ch) mod T: the threads left
-      // without work by a group smaller than T move by five warps from
-      // chunk to chunk, so no warp idles more than others
-      const uint32_t lead = (t + 160u * ch) % T;
-      for (uint32_t q = lead; q < nq_s; q += T) {
-        const uint4 e = S.ents[slot][q];
-        take(ring, acc, e.x, s.check);
-        take(ring, acc, e.y, s.check);
-        take(ring, acc, e.z, s.check);
-        take(ring, acc, e.w, s.check);
-      }
-      // a group larger than the staging slot: the rest from global memory
-      const uint4 *grp = reinterpret_cast<const uint4 *>(p.entries) + q0;
-      for (uint64_t q = nq_s + lead; q < nq; q += T) {
-        const uint4 e = ld_stream(grp + q);
-        take(ring, acc, e.x, s.check);
-        take(ring, acc, e.y, s.check);
-        take(ring, acc, e.z, s.check);
-        take(ring, acc, e.w, s.check);
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.empty[slot]);
-      g_lo = g_hi;
-      g_hi = g_next;
-    }
+    unsigned int *chk = s.check;
+    if (!ring_consume(S.r, p, nch,
+                      [&](const unsigned char *ring, uint32_t e) { take(ring, acc, e, chk); }))
+      S.bad = 1;
   }
   __syncthreads();
   const bool bad = S.bad != 0;
@@ -349,16 +400,13 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
 // the registers (Alg. 3 again, rare).  From the exact counts the block
 // derives what the gather kernel computes -- S, V, the plain estimate, the
 // feature row -- with the same operations, so both paths give the same bits.
-constexpr int kLearnSlots = 3;
 // a learned plan's groups average HB g / chunks (1650 entries for 1M hosts of
 // g = 256 over 2^24 registers); the first kLearnEntCap are staged, any rest is
 // read from global memory
 constexpr uint32_t kLearnEntCap = 2048;
 struct LearnSmem {
-  unsigned char ring[kLearnSlots][kChunkBytes];
-  uint4 ents[kLearnSlots][kLearnEntCap / 4];
+  PlanRing<kLearnEntCap> r;
   uint32_t bins[kLearnMaxHB + 1][8];  // + the spare slot of padding entries
-  uint64_t full[kLearnSlots], empty[kLearnSlots];
   double nZZ;
   int bad;
 };
@@ -368,12 +416,14 @@ __device__ __forceinline__ void take_bin(const unsigned char *ring, uint32_t *bi
                                          unsigned int *chk) {
   const uint32_t M = ring[e & (kChunkBytes - 1)];
   if (!vbk_check(M < 32u, chk, kChkPlan)) return;
-  const uint32_t lh = min(e >> kPlanChunkLog2, kLearnMaxHB);
+  // M mod 32 and the host slot at most kLearnMaxHB keep every access inside
+  // the bins whatever the entry or register value
+  const uint32_t lh = min(e >> kPlanChunkLog2, kLearnMaxHB), m = M & 31u;
   // word (M / 4) of the host's 8, swizzled by host bits 2..4: the values of
   // one warp's entries cluster, so without it their atomics fall in the
   // banks 8 lh + const; with it the bank is 8 (lh mod 4) + (M / 4 xor
   // (lh / 4 mod 8)), all 32 banks for 32 consecutive hosts
-  atomicAdd(bins + lh * 8 + ((M >> 2) ^ ((lh >> 2) & 7u)), 1u << (8u * (M & 3u)));
+  atomicAdd(bins + lh * 8 + ((m >> 2) ^ ((lh >> 2) & 7u)), 1u << (8u * (m & 3u)));
 }
 
 // Exact histogram of one host's g virtual registers (Alg. 3, gathered).
@@ -397,76 +447,22 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   const uint32_t nh = block_hosts(p, blk);
   for (uint32_t i = threadIdx.x; i < (kLearnMaxHB + 1) * 8; i += blockDim.x) (&S.bins[0][0])[i] = 0;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kLearnSlots; ++i) {
-      mbar_init(&S.full[i], 1);
-      mbar_init(&S.empty[i], kConsumerWarps);
-    }
+    ring_init(S.r);
     S.nZZ = pool_noise(d, s, c);
     S.bad = 0;
   }
   __syncthreads();
-  const uint32_t nch = p.nchunks;
+  const uint32_t nch = p.nchunks, c0 = first_chunk(blk, p.NB, nch);
   const unsigned long long *goff = p.goff + (uint64_t)blk * nch;
   if (warp == kConsumerWarps) {
-    if (lane == 0) {
-      bool ok = true;
-      uint32_t issued = 0;
-      for (uint32_t ch = 0; ch < nch; ++ch) {
-        const uint32_t slot = ch % kLearnSlots;
-        if (ch >= (uint32_t)kLearnSlots &&
-            !mbar_wait(&S.empty[slot], (ch / kLearnSlots - 1) & 1u)) {
-          ok = false;
-          break;
-        }
-        const unsigned long long ne = goff[ch + 1] - goff[ch];
-        const uint32_t ebytes = 4u * (uint32_t)(ne < kLearnEntCap ? ne : kLearnEntCap);
-        mbar_expect_tx(&S.full[slot], kChunkBytes + ebytes);
-        bulk_load_g2s(S.ring[slot], s.reg + (uint64_t)ch * kChunkBytes, kChunkBytes, &S.full[slot]);
-        if (ebytes) bulk_load_g2s(S.ents[slot], p.entries + goff[ch], ebytes, &S.full[slot]);
-        issued = ch + 1;
-      }
-      const uint32_t first = issued > (uint32_t)kLearnSlots ? issued - kLearnSlots : 0u;
-      for (uint32_t ch = first; ch < issued; ++ch)
-        if (!mbar_wait(&S.full[ch % kLearnSlots], (ch / kLearnSlots) & 1u)) ok = false;
-      if (!ok) S.bad = 1;
-    }
+    if (lane == 0 && !ring_produce(S.r, s, p, goff, c0, nch)) S.bad = 1;
   } else {
-    const uint32_t t = threadIdx.x, T = kConsumerWarps * 32;
     uint32_t *bins = &S.bins[0][0];
-    // the group offsets are read one chunk ahead: a load at the top of each
-    // chunk would put an L2 round trip on every iteration's critical path
-    unsigned long long g_lo = goff[0], g_hi = goff[1];
-    for (uint32_t ch = 0; ch < nch; ++ch) {
-      const unsigned long long g_next = ch + 2 <= nch ? goff[ch + 2] : g_hi;
-      const uint32_t slot = ch % kLearnSlots;
-      if (!mbar_wait(&S.full[slot], (ch / kLearnSlots) & 1u)) {
-        S.bad = 1;
-        break;
-      }
-      const unsigned char *ring = S.ring[slot];
-      const uint64_t q0 = g_lo / 4, nq = g_hi / 4 - q0;
-      const uint32_t nq_s = nq < kLearnEntCap / 4 ? (uint32_t)nq : kLearnEntCap / 4;
-      const uint32_t lead = (t + 160u * ch) % T;
-      for (uint32_t q = lead; q < nq_s; q += T) {
-        const uint4 e = S.ents[slot][q];
-        take_bin(ring, bins, e.x, s.check);
-        take_bin(ring, bins, e.y, s.check);
-        take_bin(ring, bins, e.z, s.check);
-        take_bin(ring, bins, e.w, s.check);
-      }
-      const uint4 *grp = reinterpret_cast<const uint4 *>(p.entries) + q0;
-      for (uint64_t q = nq_s + lead; q < nq; q += T) {
-        const uint4 e = ld_stream(grp + q);
-        take_bin(ring, bins, e.x, s.check);
-        take_bin(ring, bins, e.y, s.check);
-        take_bin(ring, bins, e.z, s.check);
-        take_bin(ring, bins, e.w, s.check);
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.empty[slot]);
-      g_lo = g_hi;
-      g_hi = g_next;
-    }
+    unsigned int *chk = s.check;
+    if (!ring_consume(S.r, p, nch, [&](const unsigned char *ring, uint32_t e) {
+          take_bin(ring, bins, e, chk);
+        }))
+      S.bad = 1;
   }
   __syncthreads();
   const bool bad = S.bad != 0;

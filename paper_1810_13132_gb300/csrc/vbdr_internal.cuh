@@ -183,13 +183,23 @@ __device__ __forceinline__ double pool_noise(const Dims &d, const DevState &s, c
 //   V > 0;  n = max(0, Z g / (Z - g) * (n_g / g - nZZ)).
 // lnv: ln v for v < kLnTab.  Every kernel that estimates calls this, so
 // their results agree bit for bit.
+// The quotient alpha_g g^2 / x (x = S 2^-32) is the costly FP64 operation
+// here (GB300's FP64 rate is low).  Where the sign of alpha_g g^2 - 2.5 g x,
+// computed with one rounding by fma, is <= 0, the exact quotient is at most
+// 2.5 g and so is its rounded value: linear counting is chosen without it.
+// Otherwise the quotient is computed and compared as written, so the
+// decision is always the one the rounded quotient makes.
 __device__ __forceinline__ double host_estimate(unsigned long long S, uint32_t V, uint32_t b,
                                                 const EstConst &c, const double *lnv, double nZZ,
                                                 double *n_g_out) {
-  const double g = (double)(1u << b);
-  double n_g = c.amm[b] / ((double)S * kTwoM32);
-  if (n_g <= 2.5 * g && V > 0)
-    n_g = g * (V < (uint32_t)kLnTab ? c.lng[b] - lnv[V] : log(g / (double)V));
+  const double g = (double)(1u << b), t = 2.5 * g, x = (double)S * kTwoM32;
+  double n_g;
+  bool lc = V > 0 && __fma_rn(-t, x, c.amm[b]) <= 0.0;
+  if (!lc) {
+    n_g = c.amm[b] / x;
+    lc = n_g <= t && V > 0;
+  }
+  if (lc) n_g = g * (V < (uint32_t)kLnTab ? c.lng[b] - lnv[V] : log(g / (double)V));
   double est = c.kz[b] * (n_g * c.inv_g[b] - nZZ);
   if (!(est > 0.0)) est = 0.0;
   if (n_g_out) *n_g_out = n_g;
