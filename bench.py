@@ -429,8 +429,8 @@ def run_ours(a):
         per_kernel[name] = {"ms": round(ms, 4), "algorithmic_bytes": int(nbytes),
                             "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
                             "traffic": _ncu_traffic(tkey.get(name, name), a.layout, a.workload)}
-    limiter = {"estimate": ("shared-memory pipe (one random byte read and one shared atomic per "
-                            "plan entry) and the plan stream: DRAM moves the plan, "
+    limiter = {"estimate": ("latency of the 3-slot copy ring (32 KiB register chunks from L2 and "
+                            "the plan's groups from DRAM): DRAM moves the plan, "
                             f"{plan_info['device_bytes'] if planned else 0} B per launch, far above "
                             "the algorithmic bytes" if planned else
                             "L1TEX/L2 rate of random 1-byte register gathers; DRAM carries only "
