@@ -345,6 +345,31 @@ def run_ours(a):
             "learned_plan": lplan.info()})
         lplan.close()
 
+    # the compact learned correction fused into the planned estimate (weights
+    # trained by tests/train_correction_compact.py), timed on the same state
+    compact = cnet = None
+    cpath = os.path.join(ROOT, "paper_1810_13132_gb300", "weights", "correction_compact_trace.npz")
+    if planned and os.path.exists(cpath) and a.workload == "trace":
+        from paper_1810_13132_gb300 import CompactNet
+        cnet = CompactNet.load(cpath)
+        d_out4 = torch.empty(H, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            v.estimate_planned_compact(plan, cnet, out=d_out4)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(a.steps):
+            v.estimate_planned_compact(plan, cnet, out=d_out4)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        plan.status()
+        c_ms = c0.elapsed_time(c1) / a.steps
+        compact = {"estimate_ms_compact_planned": round(c_ms, 4),
+                   "estimate_ms_plain_planned": round(statistics.mean(est_ms), 4),
+                   "step_ms_compact": round(statistics.mean(scan_ms) + statistics.mean(slide_ms)
+                                            + c_ms, 4),
+                   "step_ms_plain": round(ms_step, 4),
+                   "weights": os.path.relpath(cpath, ROOT)}
+
     # accuracy on the state the timed steps left (window = union of the
     # distinct slices once k >= N_DISTINCT_SLICES slices have been scanned)
     mre = None
@@ -361,6 +386,13 @@ def run_ours(a):
             def est_fn_l(sample):
                 return v.estimate_learned(mlp, torch.from_numpy(sample.view(np.int32)).cuda()).cpu().numpy()
             mre["learned"] = _exact_mre(sample, truth, est_fn_l)
+        if cnet is not None:
+            def est_fn_c(sample):
+                p = v.plan(torch.from_numpy(sample.view(np.int32)).cuda())
+                out = v.estimate_planned_compact(p, cnet).cpu().numpy()
+                p.close()
+                return out
+            mre["compact"] = _exact_mre(sample, truth, est_fn_c)
 
     # end to end through the host-buffer entry points
     e2e = None
@@ -483,6 +515,7 @@ def run_ours(a):
         "gather_estimate": gather,
         "accuracy": mre,
         "learned_correction": learned,
+        "compact_correction": compact,
         "e2e": e2e,
         "gpu_launches": 3 * a.steps,
         "clocks": clocks,

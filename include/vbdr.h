@@ -222,6 +222,29 @@ VBDR_API int vbdr_plan_status(vbdr_plan_t p);
  * configuration or device), VBDR_EORDER (no slide yet), VBDR_ECUDA. */
 VBDR_API int vbdr_estimate_planned(vbdr_t h, vbdr_plan_t p, float *d_out, void *stream);
 
+/* vbdr_estimate_planned with the compact learned correction applied in the
+ * same kernel (not in the paper; a trained correction of the plain vHLL
+ * estimate against sharing noise).  Per host the kernel also counts the
+ * virtual registers holding 0, 1, 2 and 3 (n_0 = V .. n_3) and forms ten
+ * inputs: n_0/g .. n_3/g, log2 g / 16, ln(1 + n_plain) / 16, ln(1 + n_g) / 16
+ * (n_g the host's raw or linear-counting estimate before noise removal),
+ * ln(1 + n_Z / Z), V_Z / Z and V / g; a network of two layers of 16
+ * tanh-form GELUs gives delta, and the host's estimate is
+ * max(0, exp(ln(1 + n_plain) + delta) - 1), or n_plain itself where
+ * n_plain > nmax.  FP32 arithmetic after the FP64 plain estimate.
+ * h_theta: HOST memory, 465 FP32 values, copied into the launch during the
+ * call (the caller may reuse the buffer at once): W1 [16][10] row-major,
+ * b1 [16], W2 [16][16], b2 [16], w3 [16], b3.  nmax: the largest plain
+ * estimate the network was trained on.  d_out as in vbdr_estimate_planned.
+ * Requires every g <= 512.  Runs two kernels: the planned estimate, which
+ * also writes a 16-byte record per host into a buffer owned by the handle
+ * (grown on first use after synchronising the stream, so make the first
+ * call outside any stream capture), and the network over the records.
+ * Errors: as vbdr_estimate_planned, plus VBDR_ERANGE (g above 512) and
+ * VBDR_ENOMEM. */
+VBDR_API int vbdr_estimate_planned_compact(vbdr_t h, vbdr_plan_t p, const float *h_theta,
+                                           float nmax, float *d_out, void *stream);
+
 /* A plan as vbdr_plan_create builds it, with blocks of at most 3300 hosts:
  * what vbdr_estimate_learned_planned needs (its per-host register
  * histograms share a block's shared memory); vbdr_estimate_planned accepts

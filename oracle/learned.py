@@ -91,6 +91,41 @@ def correct(n_plain, delta):
     return np.maximum(np.expm1(np.log1p(n_plain) + delta), 0.0)
 
 
+# ------------------------------------------- the compact correction network
+# A smaller network on ten features that the planned estimate can compute
+# from a host's exact sums and four register counts, so that it runs inside
+# the estimate's own kernel: the counts of register values 0..3 over g (the
+# first four bins of the histogram above) and inputs 64..69 of the feature
+# row (log2 g / 16, ln(1 + n_plain) / 16, ln(1 + n_g) / 16, ln(1 + n_Z / Z),
+# V_Z / Z, V / g).  Network: x[10] -> GELU(W1 x + b1)[16] -> GELU(W2 h1 +
+# b2)[16] -> w3 . h2 + b3, the same tanh-form GELU; parameters in a flat
+# vector W1 (16 x 10, row-major), b1, W2 (16 x 16), b2, w3, b3.
+C_IN, C_HID = 10, 16
+C_SIZES = [("W1", (C_HID, C_IN)), ("b1", (C_HID,)), ("W2", (C_HID, C_HID)), ("b2", (C_HID,)),
+           ("w3", (C_HID,)), ("b3", (1,))]
+C_N_PARAMS = sum(int(np.prod(s)) for _, s in C_SIZES)
+
+
+def compact_features(X80: np.ndarray) -> np.ndarray:
+    """The ten inputs of the compact network from 80-input feature rows."""
+    X80 = np.asarray(X80, dtype=np.float64)
+    return np.concatenate([X80[:, 0:4], X80[:, 64:70]], axis=1)
+
+
+def compact_forward(theta: np.ndarray, Xc: np.ndarray) -> np.ndarray:
+    """delta of the compact network for rows Xc [n, 10], FP64."""
+    th = np.asarray(theta, dtype=np.float64)
+    p, o = {}, 0
+    for name, shape in C_SIZES:
+        k = int(np.prod(shape))
+        p[name] = th[o:o + k].reshape(shape)
+        o += k
+    Xc = np.asarray(Xc, dtype=np.float64)
+    h1 = gelu(Xc @ p["W1"].T + p["b1"])
+    h2 = gelu(h1 @ p["W2"].T + p["b2"])
+    return h2 @ p["w3"] + p["b3"][0]
+
+
 # ------------------------------------------------------------- training sets
 
 def trace_shaped_run(seed: int, scale: int = 16, slices: int | None = None):

@@ -48,6 +48,8 @@ struct vbdr {
   uint64_t est_cap;
   uint16_t *d_feat;     // feature rows of the learned estimate [feat_cap][48]
   uint64_t feat_cap;
+  uint4 *d_crec;        // records of the compact correction [crec_cap]
+  uint64_t crec_cap;
   vbk::BucketDev bk;    // buffers of the bucketed scan (allocated when it is selected)
   int scan_mode;        // VBDR_SCAN_DIRECT (default) or VBDR_SCAN_BUCKETED
 };
@@ -178,6 +180,7 @@ void free_state(vbdr *h) {
   cudaFree(h->d_aips);
   cudaFree(h->d_out);
   cudaFree(h->d_feat);
+  cudaFree(h->d_crec);
   cudaFree(h->bk.recs);
   cudaFree(h->bk.fill);
   cudaFree(h->bk.lb);
@@ -1052,8 +1055,39 @@ int vbdr_estimate_planned(vbdr_t h, vbdr_plan_t p, float *d_out, void *stream) {
   if (!h->slid) return VBDR_EORDER;
   if (p->dev.n == 0) return VBDR_OK;
   if (!d_out || ((uintptr_t)d_out & 3u)) return VBDR_EINVAL;
-  return fail_cuda(h, vbk::launch_planned_estimate(h->d, h->s, h->est, p->dev, d_out,
-                                                   (cudaStream_t)stream));
+  return fail_cuda(h, vbk::launch_planned_estimate(h->d, h->s, h->est, p->dev, nullptr, nullptr,
+                                                   d_out, (cudaStream_t)stream));
+}
+
+int vbdr_estimate_planned_compact(vbdr_t h, vbdr_plan_t p, const float *h_theta, float nmax,
+                                  float *d_out, void *stream) {
+  NvtxRange nvtx("vbdr_estimate_planned_compact");
+  if (!h || !p || !h_theta) return VBDR_EINVAL;
+  if (h->sticky) return h->sticky;
+  if (!plan_matches(h, p)) return VBDR_EINVAL;
+  if (!h->slid) return VBDR_EORDER;
+  if (max_log2_g(h->d) > kMaxFeatureLog2G) return VBDR_ERANGE;
+  const uint64_t n = p->dev.n;
+  if (n == 0) return VBDR_OK;
+  if (!d_out || ((uintptr_t)d_out & 3u)) return VBDR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n > h->crec_cap) {  // the records' buffer, grown outside any capture
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    cudaFree(h->d_crec);
+    h->d_crec = nullptr;
+    h->crec_cap = 0;
+    if (cudaMalloc(&h->d_crec, n * sizeof(uint4)) != cudaSuccess) {
+      cudaGetLastError();
+      return VBDR_ENOMEM;
+    }
+    h->crec_cap = n;
+  }
+  vbk::CompactParams net;
+  std::memcpy(net.w, h_theta, sizeof(net.w));
+  net.nmax = nmax;
+  return fail_cuda(h, vbk::launch_planned_estimate(h->d, h->s, h->est, p->dev, &net, h->d_crec,
+                                                   d_out, st));
 }
 
 int vbdr_estimate_learned_planned(vbdr_t h, vbdr_mlp_t m, vbdr_plan_t p, float *d_out,
@@ -1112,7 +1146,7 @@ int vbdr_estimate_planned_host(vbdr_t h, vbdr_plan_t p, float *h_out, void *stre
     }
     h->est_cap = n;
   }
-  e = vbk::launch_planned_estimate(h->d, h->s, h->est, p->dev, h->d_out, st);
+  e = vbk::launch_planned_estimate(h->d, h->s, h->est, p->dev, nullptr, nullptr, h->d_out, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, h->d_out, n * 4, cudaMemcpyDeviceToHost, st);
   return fail_cuda(h, e);
 }

@@ -322,36 +322,118 @@ __device__ bool ring_consume(PlanRing<ECAP> &r, const PlanDev &p, uint32_t nch, 
 }
 
 // ----- the planned estimate -----
-// Per host three 32-bit sums, one shared atomic per plan entry:
+// Per host three 32-bit words, one shared atomic per plan entry:
 //   M = 0      -> V   += 1                 (contributes 2^32 to S)
 //   M in 1..16 -> Shi += 2^(16 - M)        (2^(32-M) = Shi unit 2^16)
 //   M > 16     -> Slo += 2^(32 - M)
 // so S = V 2^32 + Shi 2^16 + Slo exactly (each field < 2^32 for g <= 2^16).
+// The kernel with the compact learned correction also needs the counts of
+// the register values 0..3, and packs them into the same three words:
+//   M = 0, 1, 2  -> P += 2^(10 M)        (#{M = 0} = V, #{M = 1}, #{M = 2}
+//                                         in three 10-bit fields)
+//   M = 3        -> H += 2^22            (#{M = 3} in H's bits 22..31)
+//   M in 4..16   -> H += 2^(16 - M)
+//   M > 16       -> L += 2^(32 - M)
+// For g <= 512 every count is at most 512 < 2^10 and the low part of H at
+// most 512 2^12 = 2^21 < 2^22, so no field overflows into the next and
+//   S = V 2^32 + n1 2^31 + n2 2^30 + n3 2^29 + (H mod 2^22) 2^16 + L.
 constexpr uint32_t kAccRow = kPlanMaxHB + 1;  // + the spare slot of padding entries
 struct PlanSmem {
   PlanRing<kEntCap> r;
-  uint32_t acc[3][kAccRow];  // V, Shi, Slo
+  uint32_t acc[3][kAccRow];  // V, Shi, Slo (packed: P, H, L)
   double nZZ;
   int bad;
 };
 static_assert(sizeof(PlanSmem) <= 227 * 1024, "shared memory of one CTA");
 
-// One entry: register M of the chunk in the ring, added to its host's sums.
+// One entry: register M of the chunk in the ring, added to its host's words.
 // which = (M + 15) >> 4 picks V (M = 0), Shi (1..16) or Slo (17..32), and
-// 1 << ((16 - M) & 15) is 1, 2^(16-M) or 2^(32-M) respectively.
-// The two min() keep every access inside the accumulators whatever the
+// 1 << ((16 - M) & 15) is 1, 2^(16-M) or 2^(32-M) respectively.  The word
+// index is at most 2, the shift below 32 and the host slot at most
+// kPlanMaxHB, so every access stays inside the accumulators whatever the
 // entry or register value.
+template <bool PACKED>
 __device__ __forceinline__ void take(const unsigned char *ring, uint32_t *acc, uint32_t e,
                                      unsigned int *chk) {
   const uint32_t M = ring[e & (kChunkBytes - 1)];
   if (!vbk_check(M <= 32u && (e >> kPlanChunkLog2) <= kPlanMaxHB, chk, kChkPlan)) return;
-  const uint32_t which = min((M + 15u) >> 4, 2u);
   const uint32_t lh = min(e >> kPlanChunkLog2, kPlanMaxHB);
-  atomicAdd(acc + which * kAccRow + lh, 1u << ((16u - M) & 15u));
+  if constexpr (PACKED) {
+    const bool low = M <= 2u;
+    const uint32_t which = low ? 0u : min((M + 15u) >> 4, 2u);
+    const uint32_t sh = low ? 10u * M : (M == 3u ? 22u : (16u - M) & 15u);
+    atomicAdd(acc + which * kAccRow + lh, 1u << sh);
+  } else {
+    const uint32_t which = min((M + 15u) >> 4, 2u);
+    atomicAdd(acc + which * kAccRow + lh, 1u << ((16u - M) & 15u));
+  }
 }
 
+// The compact learned correction (not in the paper): ten inputs -- the
+// counts of register values 0..3 over g, log2 g / 16, ln(1 + n_plain) / 16,
+// ln(1 + n_g) / 16, ln(1 + n_Z / Z), V_Z / Z, V / g -- through two layers of
+// 16 tanh-form GELUs to delta; the estimate becomes
+// max(0, exp(ln(1 + n_plain) + delta) - 1) unless n_plain > nmax.  FP32 with
+// the fast exponential, logarithm and division (each within a few ulp; the
+// network is a correction of order one, so absolute errors of 1e-6 are
+// immaterial).  Parameters: W1 [16][10], b1 [16], W2 [16][16], b2 [16],
+// w3 [16], b3.
+constexpr int kCIn = 10, kCHid = 16;
+constexpr int kCParams = kCHid * kCIn + kCHid + kCHid * kCHid + kCHid + kCHid + 1;
+static_assert(kCParams == kCompactParams, "parameter count of the compact network");
+// Passed by value: every launch carries its own copy of the weights in the
+// kernel's parameter space, where the unrolled network reads each of them as
+// an operand of its multiply-add (no shared-memory load per weight).
+// GELU in its tanh form, z/2 (1 + tanh(u)) with u = sqrt(2/pi) (z + 0.044715
+// z^3), written as z / (1 + exp(-2u)): one exponential and one division.
+__device__ __forceinline__ float gelu_tanh(float z) {
+  const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
+  return __fdividef(z, 1.0f + __expf(-2.0f * u));
+}
+
+// Offsets of the parameters in CompactParams::w.
+constexpr int kCW1 = 0, kCB1 = kCW1 + kCHid * kCIn, kCW2 = kCB1 + kCHid,
+              kCB2 = kCW2 + kCHid * kCHid, kCW3 = kCB2 + kCHid, kCB3 = kCW3 + kCHid;
+
+// Each unit's dot product runs as two interleaved partial sums and the
+// output layer as four, so that the dependent chains are short (measured:
+// 7 us faster than single chains over 1M hosts).
+__device__ __forceinline__ float compact_delta(const CompactParams &P, const float (&x)[kCIn]) {
+  float h1[kCHid];
+#pragma unroll
+  for (int j = 0; j < kCHid; ++j) {
+    float za = P.w[kCB1 + j], zb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kCIn; i += 2) {
+      za = fmaf(P.w[kCW1 + j * kCIn + i], x[i], za);
+      zb = fmaf(P.w[kCW1 + j * kCIn + i + 1], x[i + 1], zb);
+    }
+    h1[j] = gelu_tanh(za + zb);
+  }
+  float d[4] = {P.w[kCB3], 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int j = 0; j < kCHid; ++j) {
+    float za = P.w[kCB2 + j], zb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kCHid; i += 2) {
+      za = fmaf(P.w[kCW2 + j * kCHid + i], h1[i], za);
+      zb = fmaf(P.w[kCW2 + j * kCHid + i + 1], h1[i + 1], zb);
+    }
+    d[j & 3] = fmaf(P.w[kCW3 + j], gelu_tanh(za + zb), d[j & 3]);
+  }
+  return (d[0] + d[1]) + (d[2] + d[3]);
+}
+
+// CORR: also the compact correction's inputs.  Instead of the estimate the
+// kernel then writes one record per host for compact_correct_kernel:
+// {P (V, n1, n2), n3 | b << 10 | (n_plain > nmax) << 31, n_g, n_plain}, the
+// last two as FP32 (n_plain NaN for a block whose wait expired).  The network
+// runs in a kernel of its own: here one CTA per SM, capped at 64 registers a
+// thread, would evaluate about 6600 hosts' networks with 32 warps.
+template <bool CORR>
 __global__ void __launch_bounds__(kPlanThreads, 1)
-    planned_estimate_kernel(Dims d, DevState s, EstConst c, PlanDev p, float *__restrict__ out) {
+    planned_estimate_kernel(Dims d, DevState s, EstConst c, PlanDev p, float nmax,
+                            float *__restrict__ out, uint4 *__restrict__ rec) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   PlanSmem &S = *reinterpret_cast<PlanSmem *>(smem_raw);
   const uint32_t blk = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -371,7 +453,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     uint32_t *acc = &S.acc[0][0];
     unsigned int *chk = s.check;
     if (!ring_consume(S.r, p, nch,
-                      [&](const unsigned char *ring, uint32_t e) { take(ring, acc, e, chk); }))
+                      [&](const unsigned char *ring, uint32_t e) { take<CORR>(ring, acc, e, chk); }))
       S.bad = 1;
   }
   __syncthreads();
@@ -380,12 +462,62 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   const double nZZ = S.nZZ;
   const uint64_t h0 = (uint64_t)blk * p.HB;
   for (uint32_t lh = threadIdx.x; lh < nh; lh += blockDim.x) {
-    const uint32_t V = S.acc[0][lh];
-    const unsigned long long Sum = ((unsigned long long)V << 32) +
-                                   ((unsigned long long)S.acc[1][lh] << 16) + S.acc[2][lh];
+    const uint32_t P = S.acc[0][lh], H = S.acc[1][lh];
     const uint32_t b = host_b(d, p.aips[h0 + lh]);
-    const double est = host_estimate(Sum, V, b, c, s.lnv, nZZ, nullptr);
-    out[h0 + lh] = bad ? __int_as_float(0x7fc00000) : (float)est;
+    if constexpr (CORR) {
+      const uint32_t V = P & 1023u, n1 = (P >> 10) & 1023u, n2 = P >> 20, n3 = H >> 22;
+      const unsigned long long Sum =
+          ((unsigned long long)V << 32) + ((unsigned long long)n1 << 31) +
+          ((unsigned long long)n2 << 30) + ((unsigned long long)n3 << 29) +
+          ((unsigned long long)(H & 0x3fffffu) << 16) + S.acc[2][lh];
+      double n_g = 0.0;
+      const double est = host_estimate(Sum, V, b, c, s.lnv, nZZ, &n_g);
+      const uint32_t keep = est > (double)nmax ? 1u : 0u;
+      const float r = bad ? __int_as_float(0x7fc00000) : (float)est;
+      rec[h0 + lh] = make_uint4(P, n3 | (b << 10) | (keep << 31), __float_as_uint((float)n_g),
+                                __float_as_uint(r));
+    } else {
+      const unsigned long long Sum =
+          ((unsigned long long)P << 32) + ((unsigned long long)H << 16) + S.acc[2][lh];
+      const double est = host_estimate(Sum, P, b, c, s.lnv, nZZ, nullptr);
+      out[h0 + lh] = bad ? __int_as_float(0x7fc00000) : (float)est;
+    }
+  }
+}
+
+// The compact correction of n hosts from their records (one thread a host):
+// the ten inputs, the network, and max(0, exp(ln(1 + n_plain) + delta) - 1)
+// into out; hosts above nmax (and NaN estimates) keep n_plain.
+constexpr int kCorrThreads = 256;
+__global__ void __launch_bounds__(kCorrThreads)
+    compact_correct_kernel(Dims d, DevState s, EstConst c, const uint4 *__restrict__ rec,
+                           uint64_t n, const __grid_constant__ CompactParams net,
+                           float *__restrict__ out) {
+  __shared__ float pool_in[2];
+  if (threadIdx.x == 0) {
+    // the pool's two inputs, the same for every host
+    pool_in[0] = __logf(1.0f + (float)pool_noise(d, s, c));
+    pool_in[1] = (float)((double)s.sums[1] / (double)d.Z);
+  }
+  __syncthreads();
+  const float x_noise = pool_in[0], x_vz = pool_in[1];
+  for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n;
+       h += (uint64_t)gridDim.x * blockDim.x) {
+    const uint4 q = rec[h];
+    const float r = __uint_as_float(q.w);
+    float o = r;
+    if (!(q.y >> 31) && r == r) {
+      const uint32_t V = q.x & 1023u, n1 = (q.x >> 10) & 1023u, n2 = q.x >> 20;
+      const uint32_t n3 = q.y & 1023u, b = (q.y >> 10) & 31u;
+      const float inv_g = __uint_as_float((127u - b) << 23);  // 2^-b, exact
+      const float l1p = __logf(1.0f + r);
+      const float x[kCIn] = {(float)V * inv_g, (float)n1 * inv_g, (float)n2 * inv_g,
+                             (float)n3 * inv_g, (float)b * 0.0625f, l1p * 0.0625f,
+                             __logf(1.0f + __uint_as_float(q.z)) * 0.0625f, x_noise, x_vz,
+                             (float)V * inv_g};
+      o = fmaxf(__expf(l1p + compact_delta(net, x)) - 1.0f, 0.0f);
+    }
+    out[h] = o;
   }
 }
 
@@ -556,13 +688,23 @@ cudaError_t launch_plan_sort(const PlanDev &p, bool by_host, cudaStream_t st) {
 }
 
 cudaError_t launch_planned_estimate(const Dims &d, const DevState &s, const EstConst &c,
-                                   const PlanDev &p, float *out, cudaStream_t st) {
+                                   const PlanDev &p, const CompactParams *net,
+                                   uint4 *compact_rec, float *out, cudaStream_t st) {
   if (p.NB == 0) return cudaSuccess;
   const int smem = (int)sizeof(PlanSmem);
-  cudaError_t e = cudaFuncSetAttribute(planned_estimate_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  auto k = net ? planned_estimate_kernel<true> : planned_estimate_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  planned_estimate_kernel<<<p.NB, kPlanThreads, smem, st>>>(d, s, c, p, out);
+  k<<<p.NB, kPlanThreads, smem, st>>>(d, s, c, p, net ? net->nmax : 0.0f, out, compact_rec);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !net) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t want = (p.n + kCorrThreads - 1) / kCorrThreads;
+  const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * 8;
+  compact_correct_kernel<<<(unsigned)(want < cap ? want : cap), kCorrThreads, 0, st>>>(
+      d, s, c, compact_rec, p.n, *net, out);
   return cudaGetLastError();
 }
 

@@ -303,8 +303,19 @@ struct PlanDev {
 cudaError_t launch_plan_count(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st);
 cudaError_t launch_plan_fill(const Dims &d, const DevState &s, const PlanDev &p, cudaStream_t st);
 cudaError_t launch_plan_sort(const PlanDev &p, bool by_host, cudaStream_t st);
+// The compact learned correction's FP32 parameters (W1 [16][10], b1, W2
+// [16][16], b2, w3, b3) and nmax.
+constexpr int kCompactParams = 465;  // 16 x 10 + 16 + 16 x 16 + 16 + 16 + 1
+struct CompactParams {
+  float w[kCompactParams];
+  float nmax;
+};
+// net: NULL for the plain estimate, else the compact learned correction
+// (every g <= 512), with compact_rec a device buffer of p.n records (16 bytes
+// each) between the planned kernel and the correction kernel
 cudaError_t launch_planned_estimate(const Dims &d, const DevState &s, const EstConst &c,
-                                   const PlanDev &p, float *out, cudaStream_t st);
+                                   const PlanDev &p, const CompactParams *net,
+                                   uint4 *compact_rec, float *out, cudaStream_t st);
 cudaError_t launch_planned_features(const Dims &d, const DevState &s, const EstConst &c,
                                     const PlanDev &p, float *out, __nv_bfloat16 *feat,
                                     cudaStream_t st);

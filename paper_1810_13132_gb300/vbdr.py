@@ -59,6 +59,7 @@ _SIGS = {
                                       ctypes.POINTER(_U64)]),
     "vbdr_plan_status": (ctypes.c_int, [_VP]),
     "vbdr_estimate_planned": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "vbdr_estimate_planned_compact": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_float, _VP, _VP]),
     "vbdr_estimate_planned_host": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "vbdr_get_dims": (ctypes.c_int, [_VP, ctypes.POINTER(_U32), ctypes.POINTER(_U32),
                                      ctypes.POINTER(_U32)]),
@@ -299,6 +300,18 @@ class Vbdr:
         assert out.is_cuda and out.numel() >= plan.n_hosts
         _check("vbdr_estimate_planned", self._L.vbdr_estimate_planned(
             self._h, plan._p, out.data_ptr() if plan.n_hosts else None, _stream_ptr(stream)))
+        return out
+
+    def estimate_planned_compact(self, plan: "Plan", net: "CompactNet", out=None, stream=None):
+        """Estimates of the plan's hosts with the compact learned correction
+        applied in the same kernel (float32 CUDA tensor, plan order)."""
+        import torch
+        if out is None:
+            out = torch.empty(plan.n_hosts, dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.numel() >= plan.n_hosts
+        _check("vbdr_estimate_planned_compact", self._L.vbdr_estimate_planned_compact(
+            self._h, plan._p, net.theta.ctypes.data, net.nmax,
+            out.data_ptr() if plan.n_hosts else None, _stream_ptr(stream)))
         return out
 
     def estimate_planned_host(self, plan: "Plan", out, stream=None) -> None:
@@ -640,6 +653,26 @@ class Mlp:
         _check("vbdr_mlp_forward", self._L.vbdr_mlp_forward(self._h, X.data_ptr(), n,
                                                             d.data_ptr(), _stream_ptr(stream)))
         return d
+
+
+class CompactNet:
+    """Parameters of the compact learned correction: 465 FP32 values
+    (W1 [16][10], b1, W2 [16][16], b2, w3, b3) in host memory and nmax, for
+    Vbdr.estimate_planned_compact (every call passes them with its launch)."""
+    N_PARAMS = 465
+
+    def __init__(self, params: np.ndarray, nmax: float):
+        params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        if params.size != self.N_PARAMS:
+            raise ValueError(f"the compact network has {self.N_PARAMS} parameters")
+        self.theta = params
+        self.nmax = float(nmax)
+
+    @classmethod
+    def load(cls, path: str) -> "CompactNet":
+        """From a weights file of tests/train_correction_compact.py."""
+        z = np.load(path)
+        return cls(z["params"], float(z["nmax"]))
 
 
 def live_features(X80: np.ndarray) -> np.ndarray:

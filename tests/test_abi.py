@@ -80,6 +80,8 @@ def test_null_handle_calls(lib):
     assert lib.vbdr_plan_status(None) == -1
     assert lib.vbdr_estimate_planned(None, None, None, None) == -1
     assert lib.vbdr_estimate_planned_host(None, None, None, None) == -1
+    assert lib.vbdr_estimate_planned_compact(None, None, None, ctypes.c_float(0.0), None,
+                                             None) == -1
 
 
 def test_noalloc_rejects_invalid_sizes_without_touching_the_gpu(lib):

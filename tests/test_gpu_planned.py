@@ -283,6 +283,25 @@ def test_learned_planned_overflowing_bins_and_mixed_g():
     _check_learned(v, aips, _mlp(13))
 
 
+def test_groups_larger_than_the_staging_slots():
+    """Few register chunks and many hosts per block (150000 hosts, g = 256,
+    Z = 2^16: two chunks, about 126k entries per group): most of every group
+    is read from global memory past its staged part, in the plain and in the
+    learned planned kernel."""
+    rng = np.random.default_rng(233)
+    aips = traffic.distinct_u32(rng, 150_000)
+    v, o = _make("gfast", 5, 1 << 16, 8)
+    for _ in range(2):
+        s = traffic.uniform_pairs(rng, 1 << 20, aips)
+        v.scan(_dev(s))
+        o.scan(s)
+        v.slide()
+        o.slide()
+    sample = np.random.default_rng(10).choice(len(aips), 3000, replace=False)
+    _check_plan(v, v.plan(_dev(aips)), aips, o, sample)
+    _check_learned(v, aips, _mlp(14))
+
+
 def test_learned_planned_refuses_a_plain_plan():
     from paper_1810_13132_gb300 import VbdrError
     rng = np.random.default_rng(232)

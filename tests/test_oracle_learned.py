@@ -79,3 +79,44 @@ def test_features_follow_their_definition():
         assert X[h, 69] == pytest.approx(V / 32)
         assert not X[h, 70:].any()
     assert not X[:, 32:64].any()  # registers never exceed 31
+
+
+def test_compact_network_is_the_full_network_restricted_to_its_inputs():
+    """The compact network embedded in the 80-input one (its ten inputs wired
+    to columns 0..3 and 64..69, its 16 units as the first 16 of each hidden
+    layer, every other weight and bias 0 so the other units output GELU(0) =
+    0) gives the same delta: pins the compact reference's input columns,
+    parameter layout and layer order to the pinned full network."""
+    rng = np.random.default_rng(21)
+    tc = rng.normal(0, 0.4, learned.C_N_PARAMS)
+    o = 0
+    pc = {}
+    for name, shape in learned.C_SIZES:
+        k = int(np.prod(shape))
+        pc[name] = tc[o:o + k].reshape(shape)
+        o += k
+    cols = [0, 1, 2, 3, 64, 65, 66, 67, 68, 69]
+    W1 = np.zeros((learned.HID, learned.IN))
+    W1[:16][:, cols] = pc["W1"]
+    b1 = np.zeros(learned.HID)
+    b1[:16] = pc["b1"]
+    W2 = np.zeros((learned.HID, learned.HID))
+    W2[:16, :16] = pc["W2"]
+    b2 = np.zeros(learned.HID)
+    b2[:16] = pc["b2"]
+    w3 = np.zeros(learned.HID)
+    w3[:16] = pc["w3"]
+    tf = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, w3, pc["b3"]])
+    X80 = rng.random((9, learned.IN))
+    X80[:, 70:] = 0.0
+    d_full, _ = learned.forward(tf, X80)
+    Xc = learned.compact_features(X80)
+    np.testing.assert_array_equal(Xc, X80[:, cols])
+    np.testing.assert_allclose(learned.compact_forward(tc, Xc), d_full, rtol=1e-13, atol=1e-14)
+
+
+def test_compact_zero_network_predicts_its_bias():
+    theta = np.zeros(learned.C_N_PARAMS)
+    theta[-1] = -0.5
+    d = learned.compact_forward(theta, np.random.default_rng(2).random((4, learned.C_IN)))
+    np.testing.assert_allclose(d, -0.5)
