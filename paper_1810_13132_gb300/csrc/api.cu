@@ -1071,17 +1071,17 @@ int vbdr_estimate_planned_compact(vbdr_t h, vbdr_plan_t p, const float *h_theta,
   if (n == 0) return VBDR_OK;
   if (!d_out || ((uintptr_t)d_out & 3u)) return VBDR_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  if (n > h->crec_cap) {  // the records' buffer, grown outside any capture
+  if (n + 1 > h->crec_cap) {  // the records' buffer, grown outside any capture
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail_cuda(h, e);
     cudaFree(h->d_crec);
     h->d_crec = nullptr;
     h->crec_cap = 0;
-    if (cudaMalloc(&h->d_crec, n * sizeof(uint4)) != cudaSuccess) {
+    if (cudaMalloc(&h->d_crec, (n + 1) * sizeof(uint4)) != cudaSuccess) {
       cudaGetLastError();
       return VBDR_ENOMEM;
     }
-    h->crec_cap = n;
+    h->crec_cap = n + 1;
   }
   vbk::CompactParams net;
   std::memcpy(net.w, h_theta, sizeof(net.w));

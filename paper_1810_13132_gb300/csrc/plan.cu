@@ -427,7 +427,8 @@ __device__ __forceinline__ float compact_delta(const CompactParams &P, const flo
 // CORR: also the compact correction's inputs.  Instead of the estimate the
 // kernel then writes one record per host for compact_correct_kernel:
 // {P (V, n1, n2), n3 | b << 10 | (n_plain > nmax) << 31, n_g, n_plain}, the
-// last two as FP32 (n_plain NaN for a block whose wait expired).  The network
+// last two as FP32 (n_plain NaN for a block whose wait expired), and after
+// them record n = {ln(1 + n_Z / Z), V_Z / Z} (FP32).  The network
 // runs in a kernel of its own: here one CTA per SM, capped at 64 registers a
 // thread, would evaluate about 6600 hosts' networks with 32 warps.
 template <bool CORR>
@@ -476,6 +477,10 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       const float r = bad ? __int_as_float(0x7fc00000) : (float)est;
       rec[h0 + lh] = make_uint4(P, n3 | (b << 10) | (keep << 31), __float_as_uint((float)n_g),
                                 __float_as_uint(r));
+      // record n: the pool's two inputs, the same for every host
+      if (blk == 0 && lh == 0)
+        rec[p.n] = make_uint4(__float_as_uint(__logf(1.0f + (float)nZZ)),
+                              __float_as_uint((float)((double)s.sums[1] / (double)d.Z)), 0u, 0u);
     } else {
       const unsigned long long Sum =
           ((unsigned long long)P << 32) + ((unsigned long long)H << 16) + S.acc[2][lh];
@@ -490,17 +495,11 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
 // into out; hosts above nmax (and NaN estimates) keep n_plain.
 constexpr int kCorrThreads = 256;
 __global__ void __launch_bounds__(kCorrThreads)
-    compact_correct_kernel(Dims d, DevState s, EstConst c, const uint4 *__restrict__ rec,
-                           uint64_t n, const __grid_constant__ CompactParams net,
+    compact_correct_kernel(const uint4 *__restrict__ rec, uint64_t n,
+                           const __grid_constant__ CompactParams net,
                            float *__restrict__ out) {
-  __shared__ float pool_in[2];
-  if (threadIdx.x == 0) {
-    // the pool's two inputs, the same for every host
-    pool_in[0] = __logf(1.0f + (float)pool_noise(d, s, c));
-    pool_in[1] = (float)((double)s.sums[1] / (double)d.Z);
-  }
-  __syncthreads();
-  const float x_noise = pool_in[0], x_vz = pool_in[1];
+  const uint4 pool = rec[n];  // the pool's two inputs
+  const float x_noise = __uint_as_float(pool.x), x_vz = __uint_as_float(pool.y);
   for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n;
        h += (uint64_t)gridDim.x * blockDim.x) {
     const uint4 q = rec[h];
@@ -704,7 +703,7 @@ cudaError_t launch_planned_estimate(const Dims &d, const DevState &s, const EstC
   const uint64_t want = (p.n + kCorrThreads - 1) / kCorrThreads;
   const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * 8;
   compact_correct_kernel<<<(unsigned)(want < cap ? want : cap), kCorrThreads, 0, st>>>(
-      d, s, c, compact_rec, p.n, *net, out);
+      compact_rec, p.n, *net, out);
   return cudaGetLastError();
 }
 

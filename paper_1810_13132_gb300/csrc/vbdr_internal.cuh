@@ -311,8 +311,8 @@ struct CompactParams {
   float nmax;
 };
 // net: NULL for the plain estimate, else the compact learned correction
-// (every g <= 512), with compact_rec a device buffer of p.n records (16 bytes
-// each) between the planned kernel and the correction kernel
+// (every g <= 512), with compact_rec a device buffer of p.n + 1 records (16
+// bytes each) between the planned kernel and the correction kernel
 cudaError_t launch_planned_estimate(const Dims &d, const DevState &s, const EstConst &c,
                                    const PlanDev &p, const CompactParams *net,
                                    uint4 *compact_rec, float *out, cudaStream_t st);
