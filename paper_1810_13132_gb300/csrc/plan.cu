@@ -384,44 +384,93 @@ static_assert(kCParams == kCompactParams, "parameter count of the compact networ
 // Passed by value: every launch carries its own copy of the weights in the
 // kernel's parameter space, where the unrolled network reads each of them as
 // an operand of its multiply-add (no shared-memory load per weight).
-// GELU in its tanh form, z/2 (1 + tanh(u)) with u = sqrt(2/pi) (z + 0.044715
-// z^3), written as z / (1 + exp(-2u)): one exponential and one division.
-__device__ __forceinline__ float gelu_tanh(float z) {
-  const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
-  return __fdividef(z, 1.0f + __expf(-2.0f * u));
-}
-
 // Offsets of the parameters in CompactParams::w.
 constexpr int kCW1 = 0, kCB1 = kCW1 + kCHid * kCIn, kCW2 = kCB1 + kCHid,
               kCB2 = kCW2 + kCHid * kCHid, kCW3 = kCB2 + kCHid, kCB3 = kCW3 + kCHid;
 
-// Each unit's dot product runs as two interleaved partial sums and the
-// output layer as four, so that the dependent chains are short (measured:
-// 7 us faster than single chains over 1M hosts).
-__device__ __forceinline__ float compact_delta(const CompactParams &P, const float (&x)[kCIn]) {
-  float h1[kCHid];
+// The network runs on pairs of units with Blackwell's packed FP32 arithmetic
+// (fma/mul/add .rn.f32x2: two IEEE single-precision operations per
+// instruction, each rounded as its scalar form).  The launcher reorders the
+// weights into unit pairs: W1 pair (i, p) = (W1[2p][i], W1[2p+1][i]), and so
+// on for b1, W2, b2, w3.
+struct CompactPairs {
+  float2 w1[kCIn][kCHid / 2];
+  float2 b1[kCHid / 2];
+  float2 w2[kCHid][kCHid / 2];
+  float2 b2[kCHid / 2];
+  float2 w3[kCHid / 2];
+  float b3;
+};
+
+__device__ __forceinline__ unsigned long long f2u(float2 v) {
+  return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
+}
+__device__ __forceinline__ float2 u2f(unsigned long long v) {
+  return make_float2(__uint_as_float((uint32_t)v), __uint_as_float((uint32_t)(v >> 32)));
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+  return u2f(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(d);
+}
+__device__ __forceinline__ float ex2_fast(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_fast(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// GELU in its tanh form on two units: z/2 (1 + tanh(u)), u = sqrt(2/pi)
+// (z + 0.044715 z^3), written as z / (1 + 2^(z (c1 + c2 z^2))) with
+// c1 = -2 sqrt(2/pi) log2(e), c2 = 0.044715 c1: one fast exponential and one
+// fast reciprocal per unit.
+__device__ __forceinline__ float2 gelu2(float2 z) {
+  constexpr float c1 = -2.0f * 0.7978845608028654f * 1.4426950408889634f;
+  constexpr float c2 = 0.044715f * c1;
+  const float2 t = mul2(z, fma2(mul2(z, z), make_float2(c2, c2), make_float2(c1, c1)));
+  const float2 r = make_float2(rcp_fast(1.0f + ex2_fast(t.x)), rcp_fast(1.0f + ex2_fast(t.y)));
+  return mul2(z, r);
+}
+
+__device__ __forceinline__ float compact_delta(const CompactPairs &P, const float (&x)[kCIn]) {
+  constexpr int NP = kCHid / 2;
+  float2 h1[NP];
 #pragma unroll
-  for (int j = 0; j < kCHid; ++j) {
-    float za = P.w[kCB1 + j], zb = 0.0f;
+  for (int p = 0; p < NP; ++p) h1[p] = P.b1[p];
 #pragma unroll
-    for (int i = 0; i < kCIn; i += 2) {
-      za = fmaf(P.w[kCW1 + j * kCIn + i], x[i], za);
-      zb = fmaf(P.w[kCW1 + j * kCIn + i + 1], x[i + 1], zb);
-    }
-    h1[j] = gelu_tanh(za + zb);
+  for (int i = 0; i < kCIn; ++i) {
+    const float2 xi = make_float2(x[i], x[i]);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) h1[p] = fma2(P.w1[i][p], xi, h1[p]);
   }
-  float d[4] = {P.w[kCB3], 0.0f, 0.0f, 0.0f};
 #pragma unroll
-  for (int j = 0; j < kCHid; ++j) {
-    float za = P.w[kCB2 + j], zb = 0.0f;
+  for (int p = 0; p < NP; ++p) h1[p] = gelu2(h1[p]);
+  float2 h2[NP];
 #pragma unroll
-    for (int i = 0; i < kCHid; i += 2) {
-      za = fmaf(P.w[kCW2 + j * kCHid + i], h1[i], za);
-      zb = fmaf(P.w[kCW2 + j * kCHid + i + 1], h1[i + 1], zb);
-    }
-    d[j & 3] = fmaf(P.w[kCW3 + j], gelu_tanh(za + zb), d[j & 3]);
+  for (int p = 0; p < NP; ++p) h2[p] = P.b2[p];
+#pragma unroll
+  for (int i = 0; i < kCHid; ++i) {
+    const float hi = (i & 1) ? h1[i >> 1].y : h1[i >> 1].x;
+    const float2 hb = make_float2(hi, hi);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) h2[p] = fma2(P.w2[i][p], hb, h2[p]);
   }
-  return (d[0] + d[1]) + (d[2] + d[3]);
+  float2 acc0 = make_float2(0.0f, 0.0f), acc1 = acc0;
+#pragma unroll
+  for (int p = 0; p < NP; p += 2) {
+    acc0 = fma2(P.w3[p], gelu2(h2[p]), acc0);
+    acc1 = fma2(P.w3[p + 1], gelu2(h2[p + 1]), acc1);
+  }
+  return P.b3 + ((acc0.x + acc0.y) + (acc1.x + acc1.y));
 }
 
 // CORR: also the compact correction's inputs.  Instead of the estimate the
@@ -496,7 +545,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
 constexpr int kCorrThreads = 256;
 __global__ void __launch_bounds__(kCorrThreads)
     compact_correct_kernel(const uint4 *__restrict__ rec, uint64_t n,
-                           const __grid_constant__ CompactParams net,
+                           const __grid_constant__ CompactPairs net,
                            float *__restrict__ out) {
   const uint4 pool = rec[n];  // the pool's two inputs
   const float x_noise = __uint_as_float(pool.x), x_vz = __uint_as_float(pool.y);
@@ -702,8 +751,22 @@ cudaError_t launch_planned_estimate(const Dims &d, const DevState &s, const EstC
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint64_t want = (p.n + kCorrThreads - 1) / kCorrThreads;
   const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * 8;
+  CompactPairs pr;
+  const float *w = net->w;
+  for (int i = 0; i < kCIn; ++i)
+    for (int q = 0; q < kCHid / 2; ++q)
+      pr.w1[i][q] = make_float2(w[kCW1 + (2 * q) * kCIn + i], w[kCW1 + (2 * q + 1) * kCIn + i]);
+  for (int i = 0; i < kCHid; ++i)
+    for (int q = 0; q < kCHid / 2; ++q)
+      pr.w2[i][q] = make_float2(w[kCW2 + (2 * q) * kCHid + i], w[kCW2 + (2 * q + 1) * kCHid + i]);
+  for (int q = 0; q < kCHid / 2; ++q) {
+    pr.b1[q] = make_float2(w[kCB1 + 2 * q], w[kCB1 + 2 * q + 1]);
+    pr.b2[q] = make_float2(w[kCB2 + 2 * q], w[kCB2 + 2 * q + 1]);
+    pr.w3[q] = make_float2(w[kCW3 + 2 * q], w[kCW3 + 2 * q + 1]);
+  }
+  pr.b3 = w[kCB3];
   compact_correct_kernel<<<(unsigned)(want < cap ? want : cap), kCorrThreads, 0, st>>>(
-      compact_rec, p.n, *net, out);
+      compact_rec, p.n, pr, out);
   return cudaGetLastError();
 }
 
