@@ -241,28 +241,57 @@ __device__ void ring_init(PlanRing<ECAP> &r) {
   }
 }
 
-// The producer (one thread): step ch into slot ch mod 3 once the consumers
-// released the slot's previous step.  false if a wait expired; every copy it
-// issued has landed (or its wait expired) when it returns.
+// The producer warp: step ch into slot ch mod 3 once the consumers released
+// the slot's previous step; lane 0 issues the copies.  The group offsets of
+// the chunks are read 32 steps at a time, one per lane, a batch ahead of
+// use, and handed to lane 0 by shuffles: a load per step would put an L2
+// round trip into the issue of every 16th step.  false if a wait expired;
+// every copy issued has landed (or its wait expired) when it returns.
 template <uint32_t ECAP>
 __device__ bool ring_produce(PlanRing<ECAP> &r, const DevState &s, const PlanDev &p,
                              const unsigned long long *goff, uint32_t c0, uint32_t nch) {
+  const uint32_t lane = threadIdx.x & 31u;
+  // offsets (lo, hi) of the chunk of step base + lane
+  auto fetch = [&](uint32_t base, unsigned long long &lo, unsigned long long &hi) {
+    lo = hi = 0;
+    if (base + lane < nch) {
+      const uint32_t c = (uint32_t)(((uint64_t)c0 + base + lane) % nch);
+      lo = goff[c];
+      hi = goff[c + 1];
+    }
+  };
+  unsigned long long cur_lo, cur_hi, nxt_lo, nxt_hi;
+  fetch(0, cur_lo, cur_hi);
+  fetch(32, nxt_lo, nxt_hi);
   bool ok = true;
   uint32_t issued = 0, cc = c0, slot = 0, par = 0;
   for (uint32_t ch = 0; ch < nch; ++ch) {
-    if (ch >= kRingSlots && !mbar_wait(&r.empty[slot], par ^ 1u)) {
-      ok = false;
-      break;
+    if (ch && (ch & 31u) == 0) {
+      cur_lo = nxt_lo;
+      cur_hi = nxt_hi;
+      fetch(ch + 32, nxt_lo, nxt_hi);
     }
-    const unsigned long long lo = goff[cc], ne = goff[cc + 1] - lo;
-    const uint32_t bytes = 4u * (uint32_t)(ne < ECAP ? ne : ECAP);
-    // published to the consumers by the arrive below (release) and their
-    // wait on the barrier (acquire)
-    r.lo[slot] = lo;
-    r.nq[slot] = (uint32_t)(ne >> 2);
-    mbar_expect_tx(&r.full[slot], kChunkBytes + bytes);
-    bulk_load_g2s(r.reg[slot], s.reg + (uint64_t)cc * kChunkBytes, kChunkBytes, &r.full[slot]);
-    if (bytes) bulk_load_g2s(r.ents[slot], p.entries + lo, bytes, &r.full[slot]);
+    const unsigned long long lo = __shfl_sync(0xffffffffu, cur_lo, ch & 31u);
+    const unsigned long long hi = __shfl_sync(0xffffffffu, cur_hi, ch & 31u);
+    if (ch >= kRingSlots) {
+      const bool done = mbar_wait(&r.empty[slot], par ^ 1u);
+      if (!__all_sync(0xffffffffu, done)) {
+        ok = false;
+        break;
+      }
+    }
+    if (lane == 0) {
+      const unsigned long long ne = hi - lo;
+      const uint32_t bytes = 4u * (uint32_t)(ne < ECAP ? ne : ECAP);
+      // published to the consumers by the arrive below (release) and their
+      // wait on the barrier (acquire)
+      r.lo[slot] = lo;
+      r.nq[slot] = (uint32_t)(ne >> 2);
+      mbar_expect_tx(&r.full[slot], kChunkBytes + bytes);
+      bulk_load_g2s(r.reg[slot], s.reg + (uint64_t)cc * kChunkBytes, kChunkBytes, &r.full[slot]);
+      if (bytes) bulk_load_g2s(r.ents[slot], p.entries + lo, bytes, &r.full[slot]);
+    }
+    __syncwarp();
     issued = ch + 1;
     if (++cc == nch) cc = 0;
     if (++slot == kRingSlots) {
@@ -274,7 +303,7 @@ __device__ bool ring_produce(PlanRing<ECAP> &r, const DevState &s, const PlanDev
   // block may finish
   for (uint32_t ch = issued > kRingSlots ? issued - kRingSlots : 0u; ch < issued; ++ch)
     if (!mbar_wait(&r.full[ch % kRingSlots], (ch / kRingSlots) & 1u)) ok = false;
-  return ok;
+  return __all_sync(0xffffffffu, ok);
 }
 
 // The consumers (warps 0 .. kConsumerWarps - 1): for every step, take(ring,
@@ -498,7 +527,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   const uint32_t nch = p.nchunks, c0 = first_chunk(blk, p.NB, nch);
   const unsigned long long *goff = p.goff + (uint64_t)blk * nch;
   if (warp == kConsumerWarps) {
-    if (lane == 0 && !ring_produce(S.r, s, p, goff, c0, nch)) S.bad = 1;
+    if (!ring_produce(S.r, s, p, goff, c0, nch) && lane == 0) S.bad = 1;
   } else {
     uint32_t *acc = &S.acc[0][0];
     unsigned int *chk = s.check;
@@ -635,7 +664,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   const uint32_t nch = p.nchunks, c0 = first_chunk(blk, p.NB, nch);
   const unsigned long long *goff = p.goff + (uint64_t)blk * nch;
   if (warp == kConsumerWarps) {
-    if (lane == 0 && !ring_produce(S.r, s, p, goff, c0, nch)) S.bad = 1;
+    if (!ring_produce(S.r, s, p, goff, c0, nch) && lane == 0) S.bad = 1;
   } else {
     uint32_t *bins = &S.bins[0][0];
     unsigned int *chk = s.check;
