@@ -410,18 +410,17 @@ __device__ __forceinline__ void take(const unsigned char *ring, uint32_t *acc, u
 constexpr int kCIn = 10, kCHid = 16;
 constexpr int kCParams = kCHid * kCIn + kCHid + kCHid * kCHid + kCHid + kCHid + 1;
 static_assert(kCParams == kCompactParams, "parameter count of the compact network");
-// Passed by value: every launch carries its own copy of the weights in the
-// kernel's parameter space, where the unrolled network reads each of them as
-// an operand of its multiply-add (no shared-memory load per weight).
-// Offsets of the parameters in CompactParams::w.
+// Offsets of the parameters in CompactParams::w (the API's layout).
 constexpr int kCW1 = 0, kCB1 = kCW1 + kCHid * kCIn, kCW2 = kCB1 + kCHid,
               kCB2 = kCW2 + kCHid * kCHid, kCW3 = kCB2 + kCHid, kCB3 = kCW3 + kCHid;
 
 // The network runs on pairs of units with Blackwell's packed FP32 arithmetic
-// (fma/mul/add .rn.f32x2: two IEEE single-precision operations per
+// (fma.rn.f32x2 / mul.rn.f32x2: two IEEE single-precision operations per
 // instruction, each rounded as its scalar form).  The launcher reorders the
-// weights into unit pairs: W1 pair (i, p) = (W1[2p][i], W1[2p+1][i]), and so
-// on for b1, W2, b2, w3.
+// weights into unit pairs -- W1 pair (i, p) = (W1[2p][i], W1[2p+1][i]), and
+// so on for b1, W2, b2, w3 -- and passes them by value: every launch carries
+// its own copy in the kernel's parameter space, where the unrolled network
+// reads each pair as an operand (no shared-memory load per weight).
 struct CompactPairs {
   float2 w1[kCIn][kCHid / 2];
   float2 b1[kCHid / 2];
