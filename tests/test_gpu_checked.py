@@ -23,7 +23,7 @@ import numpy as np, torch
 import oracle
 from synth import traffic
 from synth.registers import BatchedRegisters
-from paper_1810_13132_gb300 import Config, Vbdr, Mlp, live_features
+from paper_1810_13132_gb300 import CompactNet, Config, Vbdr, Mlp, live_features
 torch.cuda.set_device(0)
 SEED = 0x9E3779B97F4A7C15
 
@@ -91,6 +91,11 @@ for layout in ("gfast", "gsmall"):
     m = Mlp(seed=4)
     np.testing.assert_array_equal(v.estimate_learned_planned(m, lplan).cpu().numpy(),
                                   v.estimate_learned(m, d_aips).cpu().numpy())
+    # the compact correction's counting variant of the planned kernel; with
+    # nmax 0 every host keeps its plain estimate, bit for bit
+    keep_plain = CompactNet(np.zeros(CompactNet.N_PARAMS), 0.0)
+    np.testing.assert_array_equal(v.estimate_planned_compact(plan, keep_plain).cpu().numpy(),
+                                  v.estimate_planned(plan).cpu().numpy())
     w.merge_slice_state(v.slice_state())
     w.set_registers(v.registers_device(), v.pcsa_device() if layout == "gsmall" else None)
     close(w.estimate(d_aips).cpu().numpy(), o.estimate(gen.aips))
