@@ -21,6 +21,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "packed_f32x2.cuh"
+
 namespace vbk {
 
 constexpr int kMlpIn = 80;       // inputs of the parameter layout
@@ -69,6 +71,14 @@ constexpr float kGeluB = 0.044715f;
 __device__ __forceinline__ float gelu_f(float z) {
   const float t = tanh_fast(kGeluA * z * (1.0f + kGeluB * z * z));
   return 0.5f * z * (1.0f + t);
+}
+
+// gelu_f of two values with packed FP32 arithmetic (z/2 + z/2 tanh(u)).
+__device__ __forceinline__ float2 gelu_f2(float2 z) {
+  const float2 in = f2_fma(f2_mul(z, z), make_float2(kGeluB, kGeluB), make_float2(1.0f, 1.0f));
+  const float2 u = f2_mul(f2_mul(z, make_float2(kGeluA, kGeluA)), in);
+  const float2 hz = f2_mul(z, make_float2(0.5f, 0.5f));
+  return f2_fma(hz, make_float2(tanh_fast(u.x), tanh_fast(u.y)), hz);
 }
 
 __device__ __forceinline__ __nv_bfloat162 tanh_fast2(__nv_bfloat162 x) {
@@ -193,15 +203,21 @@ __device__ __forceinline__ float mlp_forward_warp(const __nv_bfloat16 *xs,
       }
     }
     __syncwarp();  // h1s is rewritten by the next tile
-    // output layer in FP32: delta_r = sum_j GELU(z2[r][j]) w3[j] + b3
-    part[m][0] = part[m][1] = 0.f;
+    // output layer in FP32, two columns (j, j + 1) per packed instruction:
+    // delta_r = sum_j GELU(z2[r][j]) w3[j] + b3
+    float2 pp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // rows g, g + 8
 #pragma unroll
-    for (int n = 0; n < 8; ++n)
+    for (int n = 0; n < 8; ++n) {
+      const int j = 8 * n + c;
+      const float2 b2 = *reinterpret_cast<const float2 *>(w.b2 + j);
+      const float2 w3 = *reinterpret_cast<const float2 *>(w.w3 + j);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = 8 * n + c + (q & 1);
-        part[m][q >> 1] += gelu_f(acc[n][q] + w.b2[j]) * w.w3[j];
-      }
+      for (int h = 0; h < 2; ++h)
+        pp[h] = f2_fma(gelu_f2(f2_add(make_float2(acc[n][2 * h], acc[n][2 * h + 1]), b2)), w3,
+                       pp[h]);
+    }
+    part[m][0] = pp[0].x + pp[0].y;
+    part[m][1] = pp[1].x + pp[1].y;
   }
 #pragma unroll
   for (int m = 0; m < 2; ++m)

@@ -32,6 +32,7 @@
 // its copies in flight, and the block's outputs are written as NaN.
 #include "vbdr_internal.cuh"
 #include "async_sm100.cuh"
+#include "packed_f32x2.cuh"
 
 namespace vbk {
 namespace {
@@ -430,22 +431,6 @@ struct CompactPairs {
   float b3;
 };
 
-__device__ __forceinline__ unsigned long long f2u(float2 v) {
-  return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
-}
-__device__ __forceinline__ float2 u2f(unsigned long long v) {
-  return make_float2(__uint_as_float((uint32_t)v), __uint_as_float((uint32_t)(v >> 32)));
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
-  return u2f(d);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
-  return u2f(d);
-}
 __device__ __forceinline__ float ex2_fast(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -464,9 +449,9 @@ __device__ __forceinline__ float rcp_fast(float x) {
 __device__ __forceinline__ float2 gelu2(float2 z) {
   constexpr float c1 = -2.0f * 0.7978845608028654f * 1.4426950408889634f;
   constexpr float c2 = 0.044715f * c1;
-  const float2 t = mul2(z, fma2(mul2(z, z), make_float2(c2, c2), make_float2(c1, c1)));
+  const float2 t = f2_mul(z, f2_fma(f2_mul(z, z), make_float2(c2, c2), make_float2(c1, c1)));
   const float2 r = make_float2(rcp_fast(1.0f + ex2_fast(t.x)), rcp_fast(1.0f + ex2_fast(t.y)));
-  return mul2(z, r);
+  return f2_mul(z, r);
 }
 
 __device__ __forceinline__ float compact_delta(const CompactPairs &P, const float (&x)[kCIn]) {
@@ -478,7 +463,7 @@ __device__ __forceinline__ float compact_delta(const CompactPairs &P, const floa
   for (int i = 0; i < kCIn; ++i) {
     const float2 xi = make_float2(x[i], x[i]);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) h1[p] = fma2(P.w1[i][p], xi, h1[p]);
+    for (int p = 0; p < NP; ++p) h1[p] = f2_fma(P.w1[i][p], xi, h1[p]);
   }
 #pragma unroll
   for (int p = 0; p < NP; ++p) h1[p] = gelu2(h1[p]);
@@ -490,13 +475,13 @@ __device__ __forceinline__ float compact_delta(const CompactPairs &P, const floa
     const float hi = (i & 1) ? h1[i >> 1].y : h1[i >> 1].x;
     const float2 hb = make_float2(hi, hi);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) h2[p] = fma2(P.w2[i][p], hb, h2[p]);
+    for (int p = 0; p < NP; ++p) h2[p] = f2_fma(P.w2[i][p], hb, h2[p]);
   }
   float2 acc0 = make_float2(0.0f, 0.0f), acc1 = acc0;
 #pragma unroll
   for (int p = 0; p < NP; p += 2) {
-    acc0 = fma2(P.w3[p], gelu2(h2[p]), acc0);
-    acc1 = fma2(P.w3[p + 1], gelu2(h2[p + 1]), acc1);
+    acc0 = f2_fma(P.w3[p], gelu2(h2[p]), acc0);
+    acc1 = f2_fma(P.w3[p + 1], gelu2(h2[p + 1]), acc1);
   }
   return P.b3 + ((acc0.x + acc0.y) + (acc1.x + acc1.y));
 }

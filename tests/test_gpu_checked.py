@@ -94,8 +94,8 @@ for layout in ("gfast", "gsmall"):
     # the compact correction's counting variant of the planned kernel; with
     # nmax 0 every host keeps its plain estimate, bit for bit
     keep_plain = CompactNet(np.zeros(CompactNet.N_PARAMS), 0.0)
-    np.testing.assert_array_equal(v.estimate_planned_compact(plan, keep_plain).cpu().numpy(),
-                                  v.estimate_planned(plan).cpu().numpy())
+    np.testing.assert_array_equal(v.estimate_planned_compact(lplan, keep_plain).cpu().numpy(),
+                                  v.estimate_planned(lplan).cpu().numpy())
     w.merge_slice_state(v.slice_state())
     w.set_registers(v.registers_device(), v.pcsa_device() if layout == "gsmall" else None)
     close(w.estimate(d_aips).cpu().numpy(), o.estimate(gen.aips))
