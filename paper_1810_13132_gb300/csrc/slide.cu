@@ -50,18 +50,14 @@ __device__ __forceinline__ uint32_t shr(uint32_t x) {
   return __umulhi(x, 1u << (32 - S));
 }
 
-// Saturating +1 of every field of one word.
+// Saturating +1 of every field of one word.  A field is all ones exactly
+// when adding 1 to its low W-1 bits carries into its top bit while that top
+// bit is set: with the top bits masked off first, no carry leaves a field.
 template <int W>
 __device__ __forceinline__ uint32_t sat_inc(uint32_t x) {
-  uint32_t all = x;
-  if constexpr (W >= 2) all &= shr<1>(x);
-  if constexpr (W >= 3) all &= shr<2>(x);
-  if constexpr (W >= 4) all &= shr<3>(x);
-  if constexpr (W >= 5) all &= shr<4>(x);
-  if constexpr (W >= 6) all &= shr<5>(x);
-  if constexpr (W >= 7) all &= shr<6>(x);
-  if constexpr (W >= 8) all &= shr<7>(x);
-  return x + (Fields<W>::LSB & ~all);
+  constexpr uint32_t L = Fields<W>::LSB, H = L << (W - 1);
+  const uint32_t full = ((x & ~H) + L) & x & H;  // top bit of every all-ones field
+  return x + (L ^ (full >> (W - 1)));
 }
 
 // Bit f*W set for every field f of x with value < k (an active DR).
