@@ -15,13 +15,12 @@
 // Streaming layout: each thread owns 4 consecutive BDRs and moves them with
 // 16-byte accesses -- one uint4 per DRV plane, one uint4 of bsLBP1, one
 // 4-byte store of the 4 registers -- so a warp moves 512 contiguous bytes
-// per plane.  The field arithmetic is SWAR on whole words:
-//   saturating +1 : a field is incremented unless all its w bits are set,
-//                   so no carry crosses a field;
-//   active test   : even and odd fields are split apart so that every field
-//                   has a w-bit zero gap above it; OR-ing a guard bit into the
-//                   gap and subtracting k from every field leaves the guard
-//                   set exactly for the fields with DR >= k (inactive).
+// per plane.  The field arithmetic is SWAR on whole words, both tests built
+// on one carry-masked add (every field's low w-1 bits, top bits off, so no
+// carry leaves a field):
+//   saturating +1 : a field is incremented unless all its w bits are set;
+//   active test   : DR >= k (inactive) exactly when DR + 2^w - k carries out
+//                   of the field.
 #include "vbdr_internal.cuh"
 
 namespace vbk {
@@ -31,24 +30,15 @@ constexpr int kSlideThreads = 256;
 
 template <int W>
 struct Fields {
-  static constexpr uint32_t F = 32 / W;               // fields per word
-  static constexpr uint32_t FM = (1u << W) - 1u;      // one field
-  static constexpr uint32_t lsb(uint32_t parity) {    // LSB of fields f%2==parity
+  static constexpr uint32_t F = 32 / W;           // fields per word
+  static constexpr uint32_t FM = (1u << W) - 1u;  // one field
+  static constexpr uint32_t lsb() {      // the lowest bit of every field
     uint32_t m = 0;
-    for (uint32_t f = parity; f < F; f += 2) m |= 1u << (f * W);
+    for (uint32_t f = 0; f < F; ++f) m |= 1u << (f * W);
     return m;
   }
-  static constexpr uint32_t LSB = lsb(0) | lsb(1);
-  static constexpr uint32_t EVEN = lsb(0) * FM;       // all bits of even fields
+  static constexpr uint32_t LSB = lsb();
 };
-
-// x >> s computed as the high word of x * 2^(32-s): the multiply pipe is
-// otherwise idle here while the logic pipe carries the masks.
-template <int S>
-__device__ __forceinline__ uint32_t shr(uint32_t x) {
-  static_assert(S >= 1 && S <= 31, "shift");
-  return __umulhi(x, 1u << (32 - S));
-}
 
 // Saturating +1 of every field of one word.  A field is all ones exactly
 // when adding 1 to its low W-1 bits carries into its top bit while that top
@@ -60,29 +50,35 @@ __device__ __forceinline__ uint32_t sat_inc(uint32_t x) {
   return x + (L ^ (full >> (W - 1)));
 }
 
-// Bit f*W set for every field f of x with value < k (an active DR).
+// The test DR < k (an active DR) on every field at once.  With c = 2^W - k,
+// a field holds at least k exactly when x_f + c carries out of the field.
+// The low W-1 bits of every field are added with the top bits masked off
+// (no carry leaves a field), which gives the carry into each top bit; the
+// carry out is then the majority of that carry, the field's top bit and
+// c's top bit.  KTest holds c's low bits replicated into every field and
+// the field tops if c's top bit is set (else 0).
+struct KTest {
+  uint32_t cl;  // (c mod 2^(W-1)) in every field
+  uint32_t cm;  // every field's top bit if c >= 2^(W-1), else 0
+};
+
+// Top bit f*W + W - 1 set for every field f of x with value < k.
 template <int W>
-__device__ __forceinline__ uint32_t active_fields(uint32_t x, uint32_t krep_even) {
-  constexpr uint32_t EVEN = Fields<W>::EVEN;
-  constexpr uint32_t GUARD = Fields<W>::lsb(0) << W;  // bit just above each even field
-  const uint32_t e = x & EVEN;
-  const uint32_t o = shr<W>(x) & EVEN;
-  const uint32_t te = (e | GUARD) - krep_even;  // guard survives iff field >= k
-  const uint32_t to = (o | GUARD) - krep_even;
-  const uint32_t ae = ~te & GUARD;              // active even fields, at f*W + W
-  const uint32_t ao = ~to & GUARD;              // active odd fields, at f*W
-  // an odd field count leaves a phantom field above the last one: drop it
-  return (shr<W>(ae) | ao) & Fields<W>::LSB;
+__device__ __forceinline__ uint32_t active_fields(uint32_t x, KTest kt) {
+  constexpr uint32_t H = Fields<W>::LSB << (W - 1);
+  const uint32_t t = (x & ~H) + kt.cl;
+  const uint32_t carry = (x & t) | (kt.cm & (x | t));
+  return H & ~carry;
 }
 
 // Alg. 2 on one BDR whose P words are w[0..P): the largest LBP1 r in 1..R
 // with DR[r] < k, else 0.  Fields past R hold 2^w - 1 >= k: never active.
 template <int W, int P>
-__device__ __forceinline__ uint32_t register_of(const uint32_t (&w)[P], uint32_t krep_even) {
+__device__ __forceinline__ uint32_t register_of(const uint32_t (&w)[P], KTest kt) {
   uint32_t reg = 0;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    const uint32_t a = active_fields<W>(w[p], krep_even);
+    const uint32_t a = active_fields<W>(w[p], kt);
     if (a) reg = (uint32_t)p * Fields<W>::F + (31u - (uint32_t)__clz(a)) / W + 1u;
   }
   return reg;
@@ -106,12 +102,12 @@ __device__ __forceinline__ void set_dr_of_top_bit(uint32_t (&w)[PMAX], uint32_t 
 // inactive one, i.e. the index of the bitmap's lowest unset position.
 // Fields past R are never active, so the count stops at R.
 template <int W, int P>
-__device__ __forceinline__ uint32_t pcsa_of(const uint32_t (&w)[P], uint32_t krep_even) {
+__device__ __forceinline__ uint32_t pcsa_of(const uint32_t (&w)[P], KTest kt) {
   uint32_t n = 0;
   bool run = true;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    const uint32_t inactive = ~active_fields<W>(w[p], krep_even) & Fields<W>::LSB;
+    const uint32_t inactive = ~active_fields<W>(w[p], kt) & (Fields<W>::LSB << (W - 1));
     if (run) {
       if (inactive) {
         n += (uint32_t)(__ffs(inactive) - 1) / W;
@@ -126,15 +122,15 @@ __device__ __forceinline__ uint32_t pcsa_of(const uint32_t (&w)[P], uint32_t kre
 
 template <int W, int P, bool GFAST>
 __device__ __forceinline__ uint32_t slide_one(uint32_t (&w)[P], uint32_t bsv,
-                                              uint32_t krep_even, uint32_t *pcsa) {
+                                              KTest kt, uint32_t *pcsa) {
   if constexpr (GFAST) {
 #pragma unroll
     for (int p = 0; p < P; ++p) w[p] = sat_inc<W>(w[p]);
     set_dr_of_top_bit<W, P>(w, bsv);
-    return register_of<W, P>(w, krep_even);
+    return register_of<W, P>(w, kt);
   } else {
-    const uint32_t reg = register_of<W, P>(w, krep_even);
-    *pcsa = pcsa_of<W, P>(w, krep_even);
+    const uint32_t reg = register_of<W, P>(w, kt);
+    *pcsa = pcsa_of<W, P>(w, kt);
 #pragma unroll
     for (int p = 0; p < P; ++p) w[p] = sat_inc<W>(w[p]);
     return reg;
@@ -151,7 +147,7 @@ __device__ __forceinline__ void set_comp(uint4 &v, int c, uint32_t x) {
 // LAY: kLayoutGfast / kLayoutGsmall / kLayoutSerial
 template <int W, int P, int LAY>
 __global__ void __launch_bounds__(kSlideThreads)
-    slide_kernel(Dims d, DevState s, uint32_t krep_even) {
+    slide_kernel(Dims d, DevState s, KTest kt) {
   constexpr bool GFAST = LAY != kLayoutGsmall;  // fold a slice maximum (Alg. 1 / 6)
   unsigned long long S = 0, V = 0, L = 0, Pc = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -183,7 +179,7 @@ __global__ void __launch_bounds__(kSlideThreads)
 #pragma unroll
       for (int p = 0; p < P; ++p) w[p] = comp(v[p], c);
       uint32_t pc = 0;
-      const uint32_t reg = slide_one<W, P, GFAST>(w, comp(bsq, c), krep_even, &pc);
+      const uint32_t reg = slide_one<W, P, GFAST>(w, comp(bsq, c), kt, &pc);
 #pragma unroll
       for (int p = 0; p < P; ++p) set_comp(v[p], c, w[p]);
       regs |= reg << (8 * c);
@@ -216,7 +212,7 @@ __global__ void __launch_bounds__(kSlideThreads)
     if constexpr (LAY == kLayoutGfast) bsv = s.bs[j];
     if constexpr (LAY == kLayoutSerial) bsv = s.now[j] ? 1u << (s.now[j] - 1u) : 0u;
     uint32_t pc = 0;
-    const uint32_t reg = slide_one<W, P, GFAST>(w, bsv, krep_even, &pc);
+    const uint32_t reg = slide_one<W, P, GFAST>(w, bsv, kt, &pc);
 #pragma unroll
     for (int p = 0; p < P; ++p) s.drv[(uint64_t)p * d.Zs + j] = w[p];
     if (LAY == kLayoutGfast && bsv) s.bs[j] = 0u;
@@ -278,9 +274,10 @@ cudaError_t launch_slide_l(const Dims &d, const DevState &s, cudaStream_t st) {
   uint64_t grid = (uint64_t)sms * per_sm;
   if (want < grid) grid = want ? want : 1;
   // k replicated into every even field (the subtrahend of the active test)
-  uint32_t krep = 0;
-  for (uint32_t f = 0; f < Fields<W>::F; f += 2) krep |= d.k << (f * W);
-  slide_kernel<W, P, LAY><<<(unsigned)grid, kSlideThreads, 0, st>>>(d, s, krep);
+  // the DR < k test's constants for c = 2^W - k
+  const uint32_t c = (1u << W) - d.k, H = Fields<W>::LSB << (W - 1);
+  const KTest kt{(c & ((1u << (W - 1)) - 1u)) * Fields<W>::LSB, (c >> (W - 1)) & 1u ? H : 0u};
+  slide_kernel<W, P, LAY><<<(unsigned)grid, kSlideThreads, 0, st>>>(d, s, kt);
   return cudaGetLastError();
 }
 
