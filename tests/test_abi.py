@@ -114,3 +114,21 @@ def test_oracle_and_library_share_no_source():
         if f.endswith((".c", ".py")):
             refs = code_refs(os.path.join(ROOT, "oracle", f))
             assert "paper_1810_13132_gb300" not in refs and "vbdr.h" not in refs, f
+
+
+def test_compact_net_parameters(tmp_path):
+    """CompactNet holds exactly the 465 FP32 parameters of the compact
+    correction (host memory, passed with every launch) and its nmax."""
+    import numpy as np
+    from paper_1810_13132_gb300 import CompactNet
+    with pytest.raises(ValueError):
+        CompactNet(np.zeros(464), 1.0)
+    theta = np.arange(465, dtype=np.float64) / 7.0
+    path = tmp_path / "net.npz"
+    np.savez(path, params=theta.astype(np.float32), nmax=np.float32(123.5))
+    net = CompactNet.load(str(path))
+    assert net.theta.dtype == np.float32 and net.theta.flags["C_CONTIGUOUS"]
+    np.testing.assert_array_equal(net.theta, theta.astype(np.float32))
+    assert net.nmax == 123.5
+    from oracle import learned
+    assert CompactNet.N_PARAMS == learned.C_N_PARAMS
